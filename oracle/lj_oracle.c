@@ -1,0 +1,327 @@
+/*
+ * lj_oracle.c -- plain, slow, FP64 CPU reference for the truncated-shifted
+ * Lennard-Jones NVE velocity-Verlet step of the paper's molecular-dynamics
+ * case study (Sec. 4, Algorithm 1).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant with the CUDA path of this repository.
+ *
+ * Units are reduced Lennard-Jones units: sigma = epsilon = m = 1 (Sec. 4).
+ * Positions are absolute Cartesian coordinates in a periodic orthorhombic
+ * box [0,Lx) x [0,Ly) x [0,Lz); all arrays are AoS xyz, atom i at [3i..3i+2].
+ *
+ * Readings of the paper used here (each is listed with its reason in the
+ * project's design notes):
+ *   - pair force: F_abs = 24 (2 r^-12 - r^-6) / r^2, F_i += r_ij F_abs with
+ *     r_ij = r_i - r_j (Algorithm 1);
+ *   - cutoff test is inclusive, r^2 <= rc^2 (Algorithm 1);
+ *   - "truncated and shifted" (Sec. 4) means u(rc) = 0, so the energy of a
+ *     pair is u = 4 (r^-12 - r^-6) - 4 (rc^-12 - rc^-6); the force is not
+ *     shifted;
+ *   - the virial reported is the physical W = sum_{i<j} r_ij . F_ij, which is
+ *     24 times the quantity Algorithm 1 accumulates as V;
+ *   - all three axes are periodic with the minimum-image convention (the
+ *     workloads ask for a periodic box; Sec. 3 requirement (3) forbids it for
+ *     the paper's own ring, see the scheduler notes);
+ *   - step 1 of Algorithm 1 starts with F_old := -F(r_0), so the first
+ *     velocity update leaves v_0 unchanged and the loop is standard velocity
+ *     Verlet; a run of n steps ends with one more force evaluation at r_n and
+ *     the closing half kick, so the returned state is synchronised
+ *     (r_n, v_n, F_n).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG -1
+#define ORACLE_ERR_CELLS -2
+#define ORACLE_ERR_OOM -3
+
+/* Energy shift so that the pair energy vanishes at rc (Sec. 4: truncated and
+ * shifted LJ 12-6). */
+static double lj_shift(double rc)
+{
+    double rc2i = 1.0 / (rc * rc);
+    double rc6i = rc2i * rc2i * rc2i;
+    return -4.0 * (rc6i * rc6i - rc6i);
+}
+
+/* One pair at squared distance r2 <= rc^2, Algorithm 1: returns F_abs (the
+ * factor that multiplies the separation vector r_ij) and the shifted energy
+ * of the pair. */
+static void lj_pair_terms(double r2, double ushift, double *fabs_out, double *u_out)
+{
+    double r2i = 1.0 / r2;
+    double r6i = r2i * r2i * r2i;    /* sigma^6 / r^6  */
+    double r12i = r6i * r6i;         /* sigma^12 / r^12 */
+    *fabs_out = 24.0 * (2.0 * r12i - r6i) * r2i;
+    *u_out = 4.0 * (r12i - r6i) + ushift;
+}
+
+/* Minimum-image component of a separation along a periodic axis of length L. */
+static double min_image(double d, double L)
+{
+    return d - L * nearbyint(d / L);
+}
+
+/* Pair energy and radial force (positive = repulsive) of one pair at distance
+ * r; zero beyond rc.  A closed-form probe of the pair law. */
+int oracle_pair(double r, double rc, double *force_radial, double *energy)
+{
+    if (!(r > 0.0) || !(rc > 0.0) || !force_radial || !energy) return ORACLE_ERR_ARG;
+    double r2 = r * r;
+    if (r2 <= rc * rc) {
+        double fa, u;
+        lj_pair_terms(r2, lj_shift(rc), &fa, &u);
+        *force_radial = fa * r;
+        *energy = u;
+    } else {
+        *force_radial = 0.0;
+        *energy = 0.0;
+    }
+    return ORACLE_OK;
+}
+
+/* O(N^2) minimum-image sum over unordered pairs i<j, each pair applied to
+ * both atoms (Newton's third law).  F: out, 3n.  U, W: out, totals. */
+int oracle_forces_brute(int64_t n, const double *pos, const double *box, double rc,
+                        double *F, double *U, double *W)
+{
+    if (n < 0 || !pos || !box || !F || !U || !W || !(rc > 0.0)) return ORACLE_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(box[d] >= 2.0 * rc)) return ORACLE_ERR_ARG; /* minimum image needs L >= 2 rc */
+    double rc2 = rc * rc, ushift = lj_shift(rc);
+    memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    double u_sum = 0.0, w_sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx = min_image(pos[3 * i + 0] - pos[3 * j + 0], box[0]);
+            double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], box[1]);
+            double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], box[2]);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 <= rc2) {
+                double fa, u;
+                lj_pair_terms(r2, ushift, &fa, &u);
+                F[3 * i + 0] += dx * fa; F[3 * j + 0] -= dx * fa;
+                F[3 * i + 1] += dy * fa; F[3 * j + 1] -= dy * fa;
+                F[3 * i + 2] += dz * fa; F[3 * j + 2] -= dz * fa;
+                u_sum += u;
+                w_sum += r2 * fa; /* r_ij . F_ij = r^2 F_abs */
+            }
+        }
+    }
+    *U = u_sum;
+    *W = w_sum;
+    return ORACLE_OK;
+}
+
+/* Linked-cell list (a textbook cell list, Sec. 4): cells of edge
+ * l_d = L_d / floor(L_d / rc) >= rc along each axis. */
+typedef struct {
+    int nc[3];
+    double cl[3];
+    int64_t *head; /* first atom of each cell, -1 if empty */
+    int64_t *next; /* next atom in the same cell, -1 at the end */
+} cell_list;
+
+static int cell_coord(double x, double L, double cl, int nc)
+{
+    double w = x - L * floor(x / L); /* wrap into [0, L) */
+    int c = (int)floor(w / cl);
+    if (c < 0) c = 0;
+    if (c >= nc) c = nc - 1;
+    return c;
+}
+
+static int build_cells(int64_t n, const double *pos, const double *box, double rc, cell_list *cl)
+{
+    for (int d = 0; d < 3; ++d) {
+        cl->nc[d] = (int)floor(box[d] / rc);
+        if (cl->nc[d] < 3) return ORACLE_ERR_CELLS; /* 27 distinct neighbour cells need >= 3 */
+        cl->cl[d] = box[d] / cl->nc[d];
+    }
+    int64_t ncell = (int64_t)cl->nc[0] * cl->nc[1] * cl->nc[2];
+    cl->head = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    cl->next = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!cl->head || !cl->next) {
+        free(cl->head);
+        free(cl->next);
+        return ORACLE_ERR_OOM;
+    }
+    for (int64_t c = 0; c < ncell; ++c) cl->head[c] = -1;
+    /* insert in reverse so each cell lists its atoms in increasing index order */
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int cx = cell_coord(pos[3 * i + 0], box[0], cl->cl[0], cl->nc[0]);
+        int cy = cell_coord(pos[3 * i + 1], box[1], cl->cl[1], cl->nc[1]);
+        int cz = cell_coord(pos[3 * i + 2], box[2], cl->cl[2], cl->nc[2]);
+        int64_t c = ((int64_t)cx * cl->nc[1] + cy) * cl->nc[2] + cz;
+        cl->next[i] = cl->head[c];
+        cl->head[c] = i;
+    }
+    return ORACLE_OK;
+}
+
+static void free_cells(cell_list *cl)
+{
+    free(cl->head);
+    free(cl->next);
+}
+
+/* Force, half pair energy and half pair virial on atom i from the atoms of its
+ * 27 neighbour cells, as the first loop of Algorithm 1 does per molecule:
+ * every neighbour j within rc adds r_ij F_abs to F_i, half of the pair energy
+ * to U and half of the pair virial to W. */
+static void atom_from_cells(int64_t i, const double *pos, const double *box, double rc2,
+                            double ushift, const cell_list *cl, double *f3, double *u_half,
+                            double *w_half)
+{
+    int c0[3];
+    for (int d = 0; d < 3; ++d) c0[d] = cell_coord(pos[3 * i + d], box[d], cl->cl[d], cl->nc[d]);
+    double fx = 0.0, fy = 0.0, fz = 0.0, uu = 0.0, ww = 0.0;
+    for (int ox = -1; ox <= 1; ++ox)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int oz = -1; oz <= 1; ++oz) {
+                int cx = (c0[0] + ox + cl->nc[0]) % cl->nc[0];
+                int cy = (c0[1] + oy + cl->nc[1]) % cl->nc[1];
+                int cz = (c0[2] + oz + cl->nc[2]) % cl->nc[2];
+                int64_t c = ((int64_t)cx * cl->nc[1] + cy) * cl->nc[2] + cz;
+                for (int64_t j = cl->head[c]; j >= 0; j = cl->next[j]) {
+                    if (j == i) continue;
+                    double dx = min_image(pos[3 * i + 0] - pos[3 * j + 0], box[0]);
+                    double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], box[1]);
+                    double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], box[2]);
+                    double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 <= rc2) {
+                        double fa, u;
+                        lj_pair_terms(r2, ushift, &fa, &u);
+                        fx += dx * fa;
+                        fy += dy * fa;
+                        fz += dz * fa;
+                        uu += 0.5 * u;
+                        ww += 0.5 * r2 * fa;
+                    }
+                }
+            }
+    f3[0] = fx;
+    f3[1] = fy;
+    f3[2] = fz;
+    *u_half = uu;
+    *w_half = ww;
+}
+
+/* Cell-list force on every atom (27-cell stencil, directed pairs). */
+int oracle_forces_cells(int64_t n, const double *pos, const double *box, double rc, double *F,
+                        double *U, double *W)
+{
+    if (n < 0 || !pos || !box || !F || !U || !W || !(rc > 0.0)) return ORACLE_ERR_ARG;
+    cell_list cl;
+    int rcode = build_cells(n, pos, box, rc, &cl);
+    if (rcode) return rcode;
+    double rc2 = rc * rc, ushift = lj_shift(rc), u_sum = 0.0, w_sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double uh, wh;
+        atom_from_cells(i, pos, box, rc2, ushift, &cl, &F[3 * i], &uh, &wh);
+        u_sum += uh;
+        w_sum += wh;
+    }
+    free_cells(&cl);
+    *U = u_sum;
+    *W = w_sum;
+    return ORACLE_OK;
+}
+
+/* Force and per-atom half energy / half virial for a subset of atoms only
+ * (idx[0..m-1]); used to check sampled atoms of boxes too large for a full
+ * oracle pass.  F: out, 3m; u_atom, w_atom: out, m (may be NULL). */
+int oracle_forces_subset(int64_t n, const double *pos, const double *box, double rc, int64_t m,
+                         const int64_t *idx, double *F, double *u_atom, double *w_atom)
+{
+    if (n < 0 || m < 0 || !pos || !box || !idx || !F || !(rc > 0.0)) return ORACLE_ERR_ARG;
+    for (int64_t k = 0; k < m; ++k)
+        if (idx[k] < 0 || idx[k] >= n) return ORACLE_ERR_ARG;
+    cell_list cl;
+    int rcode = build_cells(n, pos, box, rc, &cl);
+    if (rcode) return rcode;
+    double rc2 = rc * rc, ushift = lj_shift(rc);
+    for (int64_t k = 0; k < m; ++k) {
+        double uh, wh;
+        atom_from_cells(idx[k], pos, box, rc2, ushift, &cl, &F[3 * k], &uh, &wh);
+        if (u_atom) u_atom[k] = uh;
+        if (w_atom) w_atom[k] = wh;
+    }
+    free_cells(&cl);
+    return ORACLE_OK;
+}
+
+static int forces_any(int use_cells, int64_t n, const double *pos, const double *box, double rc,
+                      double *F, double *U, double *W)
+{
+    return use_cells ? oracle_forces_cells(n, pos, box, rc, F, U, W)
+                     : oracle_forces_brute(n, pos, box, rc, F, U, W);
+}
+
+static double kinetic(int64_t n, const double *vel)
+{
+    double s = 0.0;
+    for (int64_t k = 0; k < 3 * n; ++k) s += vel[k] * vel[k];
+    return 0.5 * s;
+}
+
+static void wrap_positions(int64_t n, double *pos, const double *box)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * i + d];
+            if (x >= box[d] || x < 0.0) x -= box[d] * floor(x / box[d]);
+            if (x >= box[d]) x -= box[d]; /* rounding guard: keep x in [0, L) */
+            pos[3 * i + d] = x;
+        }
+}
+
+/* Velocity-Verlet NVE run (Algorithm 1) of `steps` iterations.
+ *   pos, vel: in/out, 3n; on return the synchronised state (r_n, v_n).
+ *   F:        out, 3n, the force at r_n.
+ *   obs:      out, 3 * (steps + 1) doubles (may be NULL): (U, W, KE) at
+ *             steps 0..n, each taken where r, v and F are synchronised.
+ * Positions are wrapped into the box after every update, the periodic
+ * counterpart of storing each molecule in the slice it moved to (Sec. 4.1).
+ */
+int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc, double dt,
+               int64_t steps, int use_cells, double *F, double *obs)
+{
+    if (n < 0 || steps < 0 || !pos || !vel || !box || !F || !(rc > 0.0)) return ORACLE_ERR_ARG;
+    double *f_old = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!f_old) return ORACLE_ERR_OOM;
+    wrap_positions(n, pos, box);
+    double U, W;
+    int rcode = forces_any(use_cells, n, pos, box, rc, F, &U, &W); /* F(r_0) */
+    if (rcode) {
+        free(f_old);
+        return rcode;
+    }
+    /* F_old := -F(r_0): the first velocity update leaves v_0 unchanged. */
+    for (int64_t k = 0; k < 3 * n; ++k) f_old[k] = -F[k];
+    for (int64_t s = 0; s <= steps; ++s) {
+        if (s > 0) {
+            for (int64_t k = 0; k < 3 * n; ++k) f_old[k] = F[k]; /* F_old = F_new */
+            rcode = forces_any(use_cells, n, pos, box, rc, F, &U, &W); /* F_new = F(r_s) */
+            if (rcode) break;
+        }
+        /* second loop of Algorithm 1: v += (F_new + F_old) dt / 2 -> v_s */
+        for (int64_t k = 0; k < 3 * n; ++k) vel[k] = vel[k] + (F[k] + f_old[k]) * 0.5 * dt;
+        if (obs) {
+            obs[3 * s + 0] = U;
+            obs[3 * s + 1] = W;
+            obs[3 * s + 2] = kinetic(n, vel);
+        }
+        if (s == steps) break; /* closing half kick done: state is (r_n, v_n, F_n) */
+        /* third loop of Algorithm 1: r += v dt + F_new dt^2 / 2 */
+        for (int64_t k = 0; k < 3 * n; ++k) pos[k] = pos[k] + vel[k] * dt + F[k] * 0.5 * dt * dt;
+        wrap_positions(n, pos, box);
+    }
+    free(f_old);
+    return rcode;
+}
