@@ -1,0 +1,421 @@
+"""Benchmark of the slice-streamed LJ NVE hot path on GB300.
+
+One bench "step" is one dsea_advance of MD_STEPS velocity-Verlet steps over
+the whole 1,048,576-atom box (64^3 fcc cells, rho 0.8, T* 1.5, rc 2.5,
+dt 0.005, 43 x-slices, ring schedule) -- every part of the hot path runs in
+it: force stencil, kick/drift, rebinning and the ring scheduler.  The
+default 10 timed steps make the configured 1000 NVE steps.
+
+Printed (rank 0, one JSON line): the mixed FP32/FP64 throughput in
+atom-steps/s (value), the plain FP64 form side by side, a many-box batch
+and a served stream, the roofline of the dominant kernel, the CPU oracle
+baseline, an end-to-end number through the C ABI with host buffers, and the
+SM clocks seen during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  torchrun --nproc-per-node N bench.py --gpus N   (independent replicas)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (LJ NVE, rc=2.5σ) mixed vs plain FP64; served p50/p99 latency"
+UNIT = "atom-steps/s"
+MD_STEPS = 100                     # MD steps per bench step
+PAIRS_PER_ATOM = lambda rho: rho * 4.0 * math.pi / 3.0 * 2.5 ** 3   # directed pairs within rc
+FLOPS_PER_PAIR = 27                # FP32 flops counted per directed in-cutoff pair
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
+PROFILE = os.path.join(ROOT, "profiles", "k_ring_mixed_1m.md")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---- distributed plumbing (replicas: no data-path collective) ---------------
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---- clocks during the timed region --------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- workloads -------------------------------------------------------------------
+
+def flush_l2(buf):
+    buf.add_(1.0)      # writes 256 MB > 129 MB L2
+
+
+def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, stream):
+    """Advance one box; returns (seconds over the timed steps, kernel launches,
+    per-step event times)."""
+    pos, vel, box = spec.state()
+    b = dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision, stream=stream)
+    try:
+        for _ in range(warmup):
+            b.advance(md_steps)
+        b.sync()
+        times = []
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush_l2(flush_buf)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.advance(md_steps)
+            e1.record(stream)
+            times.append((e0, e1))
+        b.sync()
+        torch.cuda.synchronize()
+        per = [a.elapsed_time(c) * 1e-3 for a, c in times]
+        launches = steps * math.ceil(md_steps / 4096)
+        info = b.info()
+        return sum(per), launches, per, info
+    finally:
+        b.close()
+
+
+def e2e_run(dsea, torch, spec, precision, steps, md_steps, stream):
+    """End to end through the C ABI: host pos/vel in, create + bin on the
+    device, advance, read positions and velocities back to host arrays."""
+    pos, vel, box = spec.state()
+    pos_h = np.ascontiguousarray(pos)
+    vel_h = np.ascontiguousarray(vel)
+    out_r = np.empty_like(pos_h)
+    out_v = np.empty_like(vel_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b = dsea.Box(pos_h, vel_h, box, n_slices=spec.n_slices, precision=precision, stream=stream)
+        b.advance(md_steps)
+        dsea.read_positions(b.h, out_r)
+        dsea.read_velocities(b.h, out_v)
+        b.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n = len(pos_h)
+    return {"value": n * md_steps * steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes),
+            "d2h_bytes_per_step": int(out_r.nbytes + out_v.nbytes)}
+
+
+def batch_run(dsea, torch, n_boxes, md_steps, stream):
+    """Many independent boxes (N log-uniform 500-50,000, rho 0.05-0.9,
+    T 0.7-3.0) advanced together in one graph-captured persistent launch."""
+    from paper_2507_11289_gb300 import inputs
+    specs = inputs.batch_specs(n_boxes=n_boxes, steps=md_steps)
+    boxes = []
+    try:
+        for s in specs:
+            pos, vel, box = s.state()
+            boxes.append(dsea.Box(pos, vel, box, precision=dsea.MIXED, stream=stream))
+        bt = dsea.batch_create([b.h for b in boxes])
+        n_atoms = sum(b.n_atoms for b in boxes)
+        dsea.batch_advance(bt, [10] * len(boxes))          # warm-up, graph capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dsea.batch_advance(bt, [md_steps] * len(boxes))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        for b in boxes:
+            b.sync()
+        dsea.batch_destroy(bt)
+        return {"value": n_atoms * md_steps / sec, "unit": UNIT, "boxes": len(boxes),
+                "atoms": n_atoms, "md_steps": md_steps, "seconds": sec,
+                "workload": f"{len(boxes)} fcc LJ boxes, N log-uniform 500-50,000, rho U(0.05,0.9), "
+                            f"T U(0.7,3.0), mixed, one graph-replayed persistent launch"}
+    finally:
+        for b in boxes:
+            b.close()
+
+
+def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100):
+    """Poisson job stream into the continuous-batching server; latency from
+    arrival (submit) to completion on the server clock."""
+    from paper_2507_11289_gb300 import inputs
+    jobs = inputs.served_stream(rate_per_s=rate, duration_s=duration, seed=seed)
+    srv = dsea.server_create(int(budget_gb * 2 ** 30),
+                             dsea.make_params(precision=dsea.MIXED), segment, 0)
+    ids = []
+    try:
+        t0 = time.perf_counter()
+        offered = 0.0
+        for job in jobs:
+            pos, vel, box = job.spec.state()
+            while time.perf_counter() - t0 < job.arrival_s:
+                time.sleep(0.0005)
+            ids.append((dsea.server_submit(srv, pos, vel, box, job.spec.steps), job.spec.n_atoms))
+            offered += job.spec.n_atoms * job.spec.steps
+        dsea.server_drain(srv)
+        wall = time.perf_counter() - t0
+        lat = []
+        for jid, n in ids:
+            _, _, _, ta, td = dsea.server_result(srv, jid, n)
+            lat.append(td - ta)
+        st = dsea.server_stats(srv)
+    finally:
+        dsea.server_destroy(srv)
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "jobs": len(ids), "rate_per_s": rate, "arrival_window_s": duration,
+            "atom_steps_per_s": st["atom_steps"] / wall, "busy_atom_steps_per_s":
+            st["atom_steps"] / max(st["busy_seconds"], 1e-9), "offered_atom_steps_per_s":
+            offered / duration, "launches": st["launches"], "budget_gb": budget_gb,
+            "workload": "Poisson arrivals; fcc LJ boxes N log-uniform 1e3-2e6, rho U(0.3,0.9), "
+                        "T U(0.8,2.5), steps log-uniform 100-10,000; mixed"}
+
+
+def profile_traffic_per_atom_step():
+    """DRAM bytes per atom-step of the ring kernel from the committed ncu
+    summary (null if absent)."""
+    try:
+        for line in open(PROFILE):
+            if line.startswith("traffic_bytes_per_atom_step:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(spec, sample_steps):
+    """The CPU oracle as it stands (plain C, one thread) on a bounded sample:
+    `sample_steps` velocity-Verlet steps of the same box."""
+    import oracle
+    pos, vel, box = spec.state()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run(pos, vel, box, steps=sample_steps)
+    dt = time.perf_counter() - t0
+    # the oracle run does sample_steps + 1 force evaluations (closing pass included)
+    return {"value": len(pos) * sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_steps} velocity-Verlet steps of the {len(pos):,}-atom box "
+                      f"({dt:.1f} s, single thread, cell-list oracle)"}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2507_11289_gb300 import inputs
+    spec = inputs.FLUID_1M
+    per = []
+    n = spec.n_atoms
+    import oracle
+    oracle.build()
+    pos, vel, box = spec.state()
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.run(pos, vel, box, steps=args.ref_md_steps)
+        if k >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    total = sum(per)
+    value = n * args.ref_md_steps * len(per) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(per), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"LJ fluid {n:,} atoms (64^3 fcc), rho 0.8, T 1.5, rc 2.5, "
+                                   f"dt 0.005; each step = {args.ref_md_steps} velocity-Verlet "
+                                   f"steps of the CPU FP64 oracle (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.ref_md_steps} oracle steps per bench step, "
+                                       f"{len(per)} timed steps, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--md-steps", type=int, default=MD_STEPS)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--ref-md-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--batch-boxes", type=int, default=512)
+    ap.add_argument("--batch-md-steps", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-window", type=float, default=8.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
+    ap.add_argument("--skip", default="", help="comma list of legs to skip: fp64,batch,serve,cpu,e2e")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    skip = set(filter(None, args.skip.split(",")))
+
+    import torch
+    from paper_2507_11289_gb300 import dsea, inputs
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dsea.load()
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.zeros(64 * 2 ** 20, dtype=torch.float32, device="cuda")   # 256 MB
+
+    spec = inputs.FLUID_1M
+    # headline: mixed, ring schedule
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        sec, launches, per, info = time_box(dsea, torch, spec, dsea.MIXED, args.steps, args.warmup,
+                                            args.md_steps, flush_buf, stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    sec_max = max_over_ranks(sec, world)
+    atom_steps = spec.n_atoms * args.md_steps * args.steps
+    value = sum_over_ranks(atom_steps, world) / sec_max
+    launch_s = sum(per) / len(per)        # one ring launch per bench step
+    flops_per_atom_step = PAIRS_PER_ATOM(spec.rho) * FLOPS_PER_PAIR
+    achieved = spec.n_atoms * args.md_steps * flops_per_atom_step / launch_s / 1e12
+    tpa = profile_traffic_per_atom_step()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None if tpa is None else tpa * spec.n_atoms * args.md_steps,
+                "kernel": "k_ring<1> (mixed)",
+                "counted": f"{FLOPS_PER_PAIR} flops x {PAIRS_PER_ATOM(spec.rho):.2f} directed "
+                           f"in-cutoff pairs per atom-step",
+                "peak_note": "FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": "LJ fluid 1,048,576 atoms (64^3 fcc), rho 0.8, T 1.5, rc 2.5, "
+                                   "dt 0.005, 43 x-slices, ring schedule, mixed FP32 pair math / "
+                                   "FP64 state",
+                       "md_steps_per_step": args.md_steps, "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{world}", "unit_shape": [info["tile_y"], info["tile_z"]],
+                       "cell_capacity": info["cell_capacity"]},
+            "gpu_launches": launches, "roofline": roofline}
+    if "fp64" not in skip:
+        sec64, _, _, _ = time_box(dsea, torch, spec, dsea.FP64, args.fp64_steps, 3, args.md_steps,
+                                  flush_buf, stream)
+        sec64 = max_over_ranks(sec64, world)
+        v64 = sum_over_ranks(spec.n_atoms * args.md_steps * args.fp64_steps, world) / sec64
+        line["fp64"] = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
+                        "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+    if "batch" not in skip:
+        line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream)
+    if "serve" not in skip:
+        line["served"] = serve_run(dsea, torch, args.serve_rate, args.serve_window, args.serve_budget_gb)
+    if "e2e" not in skip:
+        line["e2e"] = e2e_run(dsea, torch, spec, dsea.MIXED, 3, args.md_steps, stream)
+    if rank == 0 and world == 1 and "cpu" not in skip:
+        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample_steps)
+    line["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * dsea.h -- C ABI of the GB300 slice-streamed Lennard-Jones NVE library.
+ *
+ * The library advances a periodic box of Lennard-Jones molecules with the
+ * velocity-Verlet scheme of Algorithm 1 (Sec. 4), the box cut into slices
+ * perpendicular to x, each slice at least one cutoff wide (Sec. 3, Sec. 4),
+ * every slice updated from itself and its left and right neighbours
+ * (O_in = O_out = 1, Sec. 4) and the (slice, step) updates streamed in a
+ * time-skewed cyclic order through a ring of persistent on-chip stages
+ * (Sec. 3.1 data flow, Sec. 3.3 worker firing rule).
+ *
+ * Conventions for every call:
+ *  - returns DSEA_OK (0) or a negative DSEA_ERR_* code; dsea_status_string()
+ *    names it;
+ *  - host arrays passed in are read during the call and stay owned by the
+ *    caller; outputs go to caller-allocated host arrays;
+ *  - positions, velocities and forces are AoS (x, y, z) per atom, FP64, in
+ *    the original atom-ID order (atom i at [3i, 3i+2]);
+ *  - reduced LJ units: sigma = epsilon = m = 1;
+ *  - calls on one box are not thread-safe; different boxes may be driven from
+ *    different host threads;
+ *  - work is enqueued on the CUDA stream given at creation; errors raised on
+ *    the device (capacity, migration, timeout) are reported by the next call
+ *    that synchronises with the box (dsea_sync or any dsea_read_*).
+ */
+#ifndef DSEA_H
+#define DSEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DSEA_OK 0
+#define DSEA_ERR_INVALID_ARG -1 /* bad pointer, size or geometry */
+#define DSEA_ERR_OOM -2         /* device or host allocation failed */
+#define DSEA_ERR_CUDA -3        /* a CUDA runtime call failed */
+#define DSEA_ERR_TIMEOUT -4     /* a bounded device-side wait expired */
+#define DSEA_ERR_CAPACITY -5    /* a cell received more atoms than its slots */
+#define DSEA_ERR_MIGRATION -6   /* an atom moved farther than one slice in one step */
+#define DSEA_ERR_BUDGET -7      /* a served job cannot fit the memory budget */
+#define DSEA_ERR_STATE -8       /* call out of order (e.g. no kernel registered) */
+#define DSEA_ERR_NOT_FOUND -9   /* unknown job id */
+#define DSEA_ERR_NO_DEVICE -10  /* no CUDA device available */
+
+/* ---- enums ------------------------------------------------------------- */
+#define DSEA_FP64 0  /* all pair arithmetic in FP64 */
+#define DSEA_MIXED 1 /* FP32 pair arithmetic on cell-centred coordinates;
+                        FP64 absolute positions, position update, reductions */
+
+#define DSEA_KERNEL_LJ_TS 1 /* truncated-shifted LJ 12-6 (Sec. 4, Algorithm 1) */
+
+#define DSEA_SCHED_RING 0     /* one persistent launch per advance: stages pull
+                                 (slice, step) units in time-skewed cyclic order
+                                 and wait on their neighbours' completion */
+#define DSEA_SCHED_STEPWISE 1 /* one launch per step over all units (same
+                                 per-unit arithmetic, bitwise equal results) */
+
+typedef struct dsea_box dsea_box;
+typedef struct dsea_batch dsea_batch;
+typedef struct dsea_server dsea_server;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` bytes, aligned to 256 bytes,
+ * or NULL; free releases it.  NULL allocator = cudaMalloc / cudaFree. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} dsea_allocator;
+
+/* Per-box kernel parameters (the "registered kernel", Sec. 3.3). */
+typedef struct {
+    double rc;         /* cutoff radius, sigma; 2.5 in every workload (Sec. 4) */
+    double dt;         /* timestep, tau */
+    int precision;     /* DSEA_FP64 or DSEA_MIXED */
+    int schedule;      /* DSEA_SCHED_RING or DSEA_SCHED_STEPWISE */
+    int tile_y;        /* home cells per work unit along y; 0 = automatic */
+    int tile_z;        /* home cells per work unit along z; 0 = automatic */
+    int cell_capacity; /* atom slots per cell; 0 = from the density */
+    int ctas;          /* persistent stages (CTAs) for the ring; 0 = all that fit */
+} dsea_params;
+
+/* A box as the caller describes it (Sec. 4: cubic volume of edge b, but any
+ * orthorhombic box works).  n_slices = 0 means one slice per cell layer
+ * along x (the paper's choice N_S = N_xyz, Sec. 4). */
+typedef struct {
+    int n_slices;
+    double box[3];     /* edge lengths Lx, Ly, Lz */
+    int64_t n_atoms;
+    const double *pos; /* host, 3 n_atoms, any values (wrapped into the box) */
+    const double *vel; /* host, 3 n_atoms, or NULL for zero velocities */
+} dsea_box_desc;
+
+/* Observables at the box's current step, all FP64:
+ *   U  = sum over pairs i<j of the shifted pair energy (Algorithm 1's U),
+ *   W  = sum over pairs i<j of r_ij . F_ij (24 times Algorithm 1's V),
+ *   KE = 1/2 sum_i v_i^2 at the synchronised velocity v(t_step). */
+typedef struct {
+    int64_t step;
+    double U, W, KE;
+} dsea_observables;
+
+/* Geometry and memory of a box, for inspection. */
+typedef struct {
+    int n_slices, cells_per_slice_x;
+    int cells[3];
+    int tile_y, tile_z, units_per_step;
+    int cell_capacity;
+    int precision, schedule;
+    int64_t n_atoms, step;
+    size_t device_bytes;
+    double cell_edge[3];
+} dsea_box_info;
+
+/* ---- box lifecycle ----------------------------------------------------- */
+
+/* Create a box from host positions and velocities (Sec. 3, "the user
+ * provides slices of the dataset"; Sec. 4 geometry).  The box is cut into
+ * n_slices slices along x of width Lx / n_slices >= rc and into cells of edge
+ * >= rc; needs >= 3 slices and >= 3 cells per axis.  Device state is
+ * allocated by dsea_register_kernel.  `cuda_stream` is a cudaStream_t (NULL =
+ * the legacy default stream).  *out receives the handle. */
+int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator,
+                    void *cuda_stream, dsea_box **out);
+
+/* Register the per-slice kernel (Sec. 3.3: the user kernel with input and
+ * output order).  kind must be DSEA_KERNEL_LJ_TS and o_in = o_out = 1
+ * (Sec. 4); params may be NULL for rc 2.5, dt 0.005, FP64, ring schedule.
+ * Allocates the slice/cell state on the device, bins the atoms and makes
+ * the box ready to advance. */
+int dsea_register_kernel(dsea_box *box, int kind, int o_in, int o_out, const dsea_params *params);
+
+/* Advance n_steps >= 0 velocity-Verlet steps (Algorithm 1), asynchronously
+ * on the box's stream. */
+int dsea_advance(dsea_box *box, int64_t n_steps);
+
+/* Wait for the box's queued work; returns the first device-side error. */
+int dsea_sync(dsea_box *box);
+
+/* Read the current state in atom-ID order into host arrays of 3 n doubles
+ * (n must equal the box's atom count).  Positions are wrapped into the box.
+ * Velocities and forces are synchronised with the positions (a force pass
+ * at the current positions runs on first read after an advance). */
+int dsea_read_positions(dsea_box *box, double *out_xyz, int64_t n);
+int dsea_read_velocities(dsea_box *box, double *out_xyz, int64_t n);
+int dsea_read_forces(dsea_box *box, double *out_xyz, int64_t n);
+
+/* Observables at the current step (Algorithm 1's U and V, and KE). */
+int dsea_read_observables(dsea_box *box, dsea_observables *out);
+
+int dsea_box_get_info(const dsea_box *box, dsea_box_info *out);
+
+int dsea_box_destroy(dsea_box *box);
+
+/* ---- many boxes in one persistent launch -------------------------------- */
+
+/* Group n boxes (same device, same stream, same precision, all registered)
+ * so that one persistent launch advances all of them; the launch is captured
+ * once in a CUDA graph per distinct step vector and replayed.  The boxes stay
+ * owned by the caller and must outlive the batch. */
+int dsea_batch_create(dsea_box *const *boxes, int n, dsea_batch **out);
+
+/* Advance box k by steps[k] >= 0 steps, all in one launch. */
+int dsea_batch_advance(dsea_batch *batch, const int64_t *steps);
+
+int dsea_batch_destroy(dsea_batch *batch);
+
+/* ---- autotuning -------------------------------------------------------- */
+
+/* Time each candidate work-unit shape (tile_y x tile_z home cells) for
+ * trial_steps steps on a scratch copy of the box and keep the fastest; the
+ * choice is cached per (cells per axis, cell capacity, precision) and applied
+ * to the box.  The tile shape never changes a result: each atom's force is
+ * summed in the same order whatever the shape.  *chosen (may be NULL)
+ * receives the parameters in effect. */
+int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);
+
+/* ---- serving ----------------------------------------------------------- */
+
+/* A continuous-batching server: jobs (boxes with a step count) are admitted
+ * while their device state fits mem_budget_bytes, kept resident, and
+ * advanced together in persistent launches of at most segment_steps steps;
+ * jobs join and leave between launches.  A host thread drives the device. */
+int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int segment_steps,
+                       void *cuda_stream, dsea_server **out);
+
+/* Queue a job; the box description is copied.  *job_id receives its id. */
+int dsea_server_submit(dsea_server *srv, const dsea_box_desc *desc, int64_t steps,
+                       uint64_t *job_id);
+
+/* *state: 0 queued, 1 running, 2 done, or a negative error code. */
+int dsea_server_poll(dsea_server *srv, uint64_t job_id, int *state);
+
+/* Copy a finished job's final positions and velocities (3 n doubles each,
+ * atom-ID order, may be NULL) and observables, then release it.  *t_arrive,
+ * *t_done (seconds on the server clock, may be NULL) give its latency. */
+int dsea_server_result(dsea_server *srv, uint64_t job_id, double *pos, double *vel,
+                       dsea_observables *obs, double *t_arrive, double *t_done);
+
+/* Block until every submitted job is done or failed. */
+int dsea_server_drain(dsea_server *srv);
+
+/* Server clock (seconds since creation), for stamping arrivals. */
+double dsea_server_clock(const dsea_server *srv);
+
+/* Cumulative atom-steps advanced and busy device seconds. */
+int dsea_server_stats(const dsea_server *srv, double *atom_steps, double *busy_seconds,
+                      int *launches);
+
+int dsea_server_destroy(dsea_server *srv);
+
+/* ---- failure-detection testing hooks -------------------------------------- */
+
+/* No GPU fault is involved.  DSEA_DEBUG_WITHHOLD_SLICE: during the next ring
+ * advances, slice `value` never reports its first level complete, so every
+ * unit that depends on it waits until the bounded wait expires, the launch
+ * stops and the next synchronising call returns DSEA_ERR_TIMEOUT (the box is
+ * then unusable); -1 turns the hook off.  DSEA_DEBUG_WAIT_LIMIT_NS: the
+ * bounded-wait limit in nanoseconds (default 5 s). */
+#define DSEA_DEBUG_WITHHOLD_SLICE 1
+#define DSEA_DEBUG_WAIT_LIMIT_NS 2
+int dsea_debug_set(dsea_box *box, int key, int64_t value);
+
+/* ---- host-side schedule introspection (no GPU needed) ------------------- */
+
+/* The order in which the ring dispatches the units of one box: for
+ * k = 0 .. n_slices * units_per_slice * n_steps - 1, out_slice[k] and
+ * out_step[k] name the slice and relative step of the k-th unit.  Every
+ * unit's dependencies (slices j-2 .. j+2 at the previous step, periodic)
+ * come earlier in this order. */
+int dsea_ring_order(int n_slices, int units_per_slice, int64_t n_steps, int64_t start_step,
+                    int32_t *out_slice, int32_t *out_step);
+
+/* Human-readable name of a status code. */
+const char *dsea_status_string(int status);
+
+/* Library version, e.g. "0.1.0". */
+const char *dsea_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSEA_H */

@@ -1,0 +1,932 @@
+// dsea_api.cu -- host side of the C ABI declared in include/dsea.h: box
+// lifecycle, the two launch forms of an advance, read-back, many-box batches
+// replayed from CUDA graphs, the work-unit autotuner and schedule
+// introspection.
+#include "dsea_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+using dsea::BoxDev;
+
+struct dsea_batch {
+    std::vector<dsea_box *> boxes;
+    cudaStream_t stream = nullptr;
+    int precision = 0;
+    dsea::MultiPlan mp;
+    cudaEvent_t done_ev = nullptr;
+    std::map<std::vector<int64_t>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+int map_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return DSEA_OK;
+    if (e == cudaErrorMemoryAllocation) return DSEA_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return DSEA_ERR_NO_DEVICE;
+    return DSEA_ERR_CUDA;
+}
+
+int map_device_error(int code)
+{
+    switch (code) {
+    case dsea::kErrNone: return DSEA_OK;
+    case dsea::kErrCapacity: return DSEA_ERR_CAPACITY;
+    case dsea::kErrMigration: return DSEA_ERR_MIGRATION;
+    case dsea::kErrTimeout: return DSEA_ERR_TIMEOUT;
+    default: return DSEA_ERR_CUDA;
+    }
+}
+
+#define CU(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return map_cuda(e_); \
+    } while (0)
+
+void *dev_alloc(dsea_box *b, size_t bytes)
+{
+    void *p = nullptr;
+    bytes = std::max<size_t>(bytes, 256);
+    if (b->has_alloc) {
+        p = b->alloc.alloc(bytes, b->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        b->allocs.push_back(p);
+        b->device_bytes += bytes;
+    }
+    return p;
+}
+
+void dev_free_all(dsea_box *b)
+{
+    for (void *p : b->allocs) {
+        if (b->has_alloc) b->alloc.free(p, b->alloc.ctx);
+        else cudaFree(p);
+    }
+    b->allocs.clear();
+    b->device_bytes = 0;
+}
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// Fill the work-unit shape fields of hb for a (ty, tz) tile.
+bool apply_tile(BoxDev &hb, double mean_cap, int ty, int tz)
+{
+    ty = std::max(1, std::min(ty, hb.nc[1]));
+    tz = std::max(1, std::min(tz, hb.nc[2]));
+    hb.tile_y = ty;
+    hb.tile_z = tz;
+    hb.tiles_y = (hb.nc[1] + ty - 1) / ty;
+    hb.tiles_z = (hb.nc[2] + tz - 1) / tz;
+    hb.units_per_slice = hb.tiles_y * hb.tiles_z;
+    hb.staged_cells = (hb.cps + 2) * (ty + 2) * (tz + 2);
+    if (hb.staged_cells > dsea::kMaxStagedCells) return false;
+    // room for the expected stage plus a quarter, never more than every slot
+    const double expect = hb.staged_cells * mean_cap * 1.25 + 64.0;
+    const double worst = (double)hb.staged_cells * hb.cap;
+    hb.smem_atoms = (int)std::ceil(std::min(expect, worst));
+    return dsea::unit_smem_bytes(hb.precision, hb.staged_cells, hb.smem_atoms) <=
+           dsea::max_unit_smem_bytes();
+}
+
+int upload_desc(dsea_box *b)
+{
+    CU(cudaMemcpyAsync(b->db, &b->hb, sizeof(BoxDev), cudaMemcpyHostToDevice, b->stream));
+    return DSEA_OK;
+}
+
+int check_device_error(dsea_box *b)
+{
+    if (b->latched != DSEA_OK) return b->latched;
+    CU(cudaStreamSynchronize(b->stream));
+    int code = 0;
+    CU(cudaMemcpy(&code, b->hb.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code != 0) b->latched = map_device_error(code);
+    return b->latched;
+}
+
+int ring_launch_single(dsea_box *b, int64_t n)
+{
+    BoxDev &hb = b->hb;
+    const int64_t U = (int64_t)hb.n_slices * hb.units_per_slice;
+    if (n + 1 > b->step_base_cap) {
+        b->step_base_cap = std::max<int64_t>(n + 1, 1024);
+        b->d_step_base = (int64_t *)dev_alloc(b, sizeof(int64_t) * b->step_base_cap);
+        b->d_active = (int *)dev_alloc(b, sizeof(int) * b->step_base_cap);
+        if (!b->d_step_base || !b->d_active) return DSEA_ERR_OOM;
+        std::vector<int> ones(b->step_base_cap, 1);
+        CU(cudaMemcpyAsync(b->d_active, ones.data(), sizeof(int) * ones.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+    }
+    std::vector<int64_t> sb(n + 1);
+    for (int64_t s = 0; s <= n; ++s) sb[s] = s * U;
+    CU(cudaMemcpyAsync(b->d_step_base, sb.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice,
+                       b->stream));
+    const int64_t cum[2] = {0, U};
+    CU(cudaMemcpyAsync(b->d_cum, cum, sizeof(cum), cudaMemcpyHostToDevice, b->stream));
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(hb.done, 0, sizeof(unsigned) * hb.n_slices, b->stream));
+    CU(cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned long long), b->stream));
+    CU(cudaMemsetAsync(b->d_launch_err, 0, sizeof(int), b->stream));
+    dsea::RingPlan plan{};
+    plan.boxes = b->db;
+    plan.step_base = b->d_step_base;
+    plan.cum_units = b->d_cum;
+    plan.active = b->d_active;
+    plan.n_boxes = 1;
+    plan.n_steps = (int)n;
+    plan.total = n * U;
+    plan.ticket = b->d_ticket;
+    plan.err = b->d_launch_err;
+    const size_t smem = dsea::unit_smem_bytes(hb.precision, hb.staged_cells, hb.smem_atoms);
+    int ctas = b->params.ctas;
+    if (ctas <= 0) ctas = num_sms() * std::max(1, dsea::ring_ctas_per_sm(hb.precision, smem));
+    if ((int64_t)ctas > plan.total) ctas = (int)plan.total;
+    CU(dsea::launch_ring(plan, hb.precision, smem, ctas, b->stream));
+    return DSEA_OK;
+}
+
+int advance_impl(dsea_box *b, int64_t n)
+{
+    BoxDev &hb = b->hb;
+    if (n == 0) return DSEA_OK;
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    if (b->params.schedule == DSEA_SCHED_STEPWISE) {
+        for (int64_t s = 0; s < n; ++s) {
+            CU(dsea::launch_step(hb, b->db, hb.step + s, (hb.w_is_sync && s == 0) ? 1 : 0, b->stream));
+        }
+        hb.step += n;
+        hb.w_is_sync = 0;
+    } else {
+        const int64_t chunk = 4096;   // bounded plan arrays per launch
+        for (int64_t done = 0; done < n; done += chunk) {
+            const int64_t m = std::min(chunk, n - done);
+            rc = ring_launch_single(b, m);
+            if (rc) return rc;
+            hb.step += m;
+            hb.w_is_sync = 0;
+        }
+    }
+    b->outputs_valid = false;
+    return DSEA_OK;
+}
+
+int ensure_outputs(dsea_box *b)
+{
+    if (b->outputs_valid) return check_device_error(b);
+    BoxDev &hb = b->hb;
+    if (!hb.out_r) {
+        const size_t bytes = sizeof(double) * 3 * (size_t)std::max<int64_t>(hb.n_atoms, 1);
+        hb.out_r = (double *)dev_alloc(b, bytes);
+        hb.out_v = (double *)dev_alloc(b, bytes);
+        hb.out_f = (double *)dev_alloc(b, bytes);
+        if (!hb.out_r || !hb.out_v || !hb.out_f) return DSEA_ERR_OOM;
+    }
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    CU(dsea::launch_force_pass(hb, b->db, b->stream));
+    CU(dsea::launch_obs_reduce(hb.unit_obs, hb.n_slices * hb.units_per_slice, b->d_obs3, b->stream));
+    CU(cudaMemcpyAsync(b->obs3, b->d_obs3, sizeof(b->obs3), cudaMemcpyDeviceToHost, b->stream));
+    rc = check_device_error(b);
+    if (rc) return rc;
+    b->outputs_valid = true;
+    return DSEA_OK;
+}
+
+int read_array(dsea_box *b, double *out, int64_t n)
+{
+    if (!b || !out || n != b->hb.n_atoms) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    return ensure_outputs(b);
+}
+
+struct TuneKey {
+    int nc0, nc1, nc2, cps, cap, precision;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(nc0, nc1, nc2, cps, cap, precision) <
+               std::tie(o.nc0, o.nc1, o.nc2, o.cps, o.cap, o.precision);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+// Geometry, cell capacity, pair constants and work-unit shape of a box
+// (Sec. 4: slices along x of width >= rc, cells of edge >= rc); validates p
+// and fills in its automatic fields.
+int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_params &p, BoxDev &hb,
+                   double &mean_cap)
+{
+    if (!(p.rc > 0.0) || !(p.dt > 0.0) || !std::isfinite(p.rc) || !std::isfinite(p.dt))
+        return DSEA_ERR_INVALID_ARG;
+    if (p.precision != DSEA_FP64 && p.precision != DSEA_MIXED) return DSEA_ERR_INVALID_ARG;
+    if (p.schedule != DSEA_SCHED_RING && p.schedule != DSEA_SCHED_STEPWISE) return DSEA_ERR_INVALID_ARG;
+    if (p.tile_y < 0 || p.tile_z < 0 || p.cell_capacity < 0 || p.ctas < 0) return DSEA_ERR_INVALID_ARG;
+    // geometry (Sec. 4): slices along x of width >= rc, cubic-ish cells >= rc
+    int n_s = n_slices_req, cps = 1;
+    if (n_s == 0) {
+        n_s = (int)std::floor(L[0] / p.rc);
+    } else {
+        const double w = L[0] / n_s;
+        if (w < p.rc) return DSEA_ERR_INVALID_ARG;
+        cps = (int)std::floor(w / p.rc);
+    }
+    const int ncy = (int)std::floor(L[1] / p.rc), ncz = (int)std::floor(L[2] / p.rc);
+    if (n_s < 3 || cps < 1 || (int64_t)n_s * cps < 3 || ncy < 3 || ncz < 3) return DSEA_ERR_INVALID_ARG;
+    hb.n_slices = n_s;
+    hb.cps = cps;
+    hb.nc[0] = n_s * cps;
+    hb.nc[1] = ncy;
+    hb.nc[2] = ncz;
+    for (int d = 0; d < 3; ++d) {
+        hb.L[d] = L[d];
+        hb.lc[d] = L[d] / hb.nc[d];
+        hb.inv_lc[d] = 1.0 / hb.lc[d];
+        hb.lcf[d] = (float)hb.lc[d];
+    }
+    hb.n_cells = (int64_t)hb.nc[0] * hb.nc[1] * hb.nc[2];
+    if (hb.n_cells >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
+    const double vol = hb.lc[0] * hb.lc[1] * hb.lc[2];
+    const double mean = hb.n_cells > 0 ? (double)n_atoms / (double)hb.n_cells : 0.0;
+    // a cell may hold liquid at rho ~ 0.9 even in a dilute box (phase separation)
+    mean_cap = std::max(mean, 0.9 * vol);
+    int cap = p.cell_capacity;
+    if (cap <= 0) {
+        cap = (int)std::ceil(mean_cap + 6.0 * std::sqrt(mean_cap) + 6.0);
+        cap = std::max(8, (cap + 3) / 4 * 4);
+    }
+    hb.cap = cap;
+    hb.n_slots = hb.n_cells * cap;
+    if (hb.n_slots >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
+    hb.precision = p.precision;
+    hb.rc2 = p.rc * p.rc;
+    hb.rc2f = (float)hb.rc2;
+    const double rc6i = 1.0 / (hb.rc2 * hb.rc2 * hb.rc2);
+    hb.ushift = -4.0 * (rc6i * rc6i - rc6i);
+    hb.ushiftf = (float)hb.ushift;
+    hb.dt = p.dt;
+    hb.step = 0;
+    hb.w_is_sync = 1;
+    hb.withhold_slice = -1;
+    hb.wait_limit_ns = 5000000000LL;   // 5 s
+    // work-unit shape: requested, cached by the autotuner, or 4 x 4 cells
+    int ty = p.tile_y, tz = p.tile_z;
+    if (ty == 0 || tz == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find({hb.nc[0], hb.nc[1], hb.nc[2], cps, cap, p.precision});
+        if (it != g_tune_cache.end()) {
+            ty = it->second.first;
+            tz = it->second.second;
+        } else {
+            ty = ty ? ty : 4;
+            tz = tz ? tz : 4;
+        }
+    }
+    while (!apply_tile(hb, mean_cap, ty, tz)) {
+        if (ty == 1 && tz == 1) return DSEA_ERR_INVALID_ARG;   // one cell's stage does not fit
+        if (tz >= ty && tz > 1) --tz;
+        else --ty;
+    }
+    p.tile_y = hb.tile_y;
+    p.tile_z = hb.tile_z;
+    p.cell_capacity = cap;
+    hb.n_atoms = n_atoms;
+    return DSEA_OK;
+
+}
+
+
+}  // namespace
+
+extern "C" {
+
+const char *dsea_version(void) { return "0.1.0"; }
+
+const char *dsea_status_string(int s)
+{
+    switch (s) {
+    case DSEA_OK: return "ok";
+    case DSEA_ERR_INVALID_ARG: return "invalid argument";
+    case DSEA_ERR_OOM: return "out of memory";
+    case DSEA_ERR_CUDA: return "CUDA runtime error";
+    case DSEA_ERR_TIMEOUT: return "bounded device wait expired";
+    case DSEA_ERR_CAPACITY: return "cell capacity exceeded";
+    case DSEA_ERR_MIGRATION: return "atom moved farther than one slice in a step";
+    case DSEA_ERR_BUDGET: return "job exceeds the memory budget";
+    case DSEA_ERR_STATE: return "call out of order";
+    case DSEA_ERR_NOT_FOUND: return "unknown job";
+    case DSEA_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+    }
+}
+
+int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, void *cuda_stream,
+                    dsea_box **out)
+{
+    if (!desc || !out || desc->n_atoms < 0 || desc->n_slices < 0) return DSEA_ERR_INVALID_ARG;
+    if (desc->n_atoms > 0 && !desc->pos) return DSEA_ERR_INVALID_ARG;
+    if (desc->n_atoms >= (int64_t)1 << 31) return DSEA_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(desc->box[d] > 0.0) || !std::isfinite(desc->box[d])) return DSEA_ERR_INVALID_ARG;
+    if (allocator && (!allocator->alloc || !allocator->free)) return DSEA_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DSEA_ERR_NO_DEVICE;
+    }
+    dsea_box *b = new (std::nothrow) dsea_box();
+    if (!b) return DSEA_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->stream = (cudaStream_t)cuda_stream;
+    if (allocator) {
+        b->alloc = *allocator;
+        b->has_alloc = true;
+    }
+    b->n_slices_req = desc->n_slices;
+    for (int d = 0; d < 3; ++d) b->L[d] = desc->box[d];
+    b->hb.n_atoms = desc->n_atoms;
+    b->pos0.assign(desc->pos, desc->pos + 3 * desc->n_atoms);
+    b->has_vel = desc->vel != nullptr;
+    if (b->has_vel) b->vel0.assign(desc->vel, desc->vel + 3 * desc->n_atoms);
+    for (double x : b->pos0)
+        if (!std::isfinite(x)) {
+            delete b;
+            return DSEA_ERR_INVALID_ARG;
+        }
+    *out = b;
+    return DSEA_OK;
+}
+
+int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_params *params)
+{
+    if (!b) return DSEA_ERR_INVALID_ARG;
+    if (b->registered) return DSEA_ERR_STATE;
+    if (kind != DSEA_KERNEL_LJ_TS || o_in != 1 || o_out != 1) return DSEA_ERR_INVALID_ARG;
+    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0};
+    if (params) p = *params;
+    CU(cudaSetDevice(b->device));
+    BoxDev &hb = b->hb;
+    int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
+    if (rc0) return rc0;
+    const int n_s = hb.n_slices;
+    b->params = p;
+
+    // device state
+    b->db = (BoxDev *)dev_alloc(b, sizeof(BoxDev));
+    hb.err = (int *)dev_alloc(b, sizeof(int));
+    hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * n_s);
+    const int64_t max_units = hb.n_cells;   // any tile shape has at most one unit per cell
+    hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * 3 * (size_t)max_units);
+    b->d_obs3 = (double *)dev_alloc(b, sizeof(double) * 3);
+    b->d_cum = (int64_t *)dev_alloc(b, sizeof(int64_t) * 2);
+    b->d_ticket = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long));
+    b->d_launch_err = (int *)dev_alloc(b, sizeof(int));
+    if (!b->db || !hb.err || !hb.done || !hb.unit_obs || !b->d_obs3 || !b->d_cum || !b->d_ticket ||
+        !b->d_launch_err)
+        return DSEA_ERR_OOM;
+    for (int q = 0; q < 2; ++q) {
+        hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * hb.n_cells);
+        hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
+        hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        hb.q[q] = nullptr;
+        if (p.precision == DSEA_MIXED) hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
+        if (!hb.cnt[q] || !hb.id[q] || !hb.r[q] || !hb.v[q] ||
+            (p.precision == DSEA_MIXED && !hb.q[q]))
+            return DSEA_ERR_OOM;
+        CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * hb.n_cells, b->stream));
+    }
+    CU(cudaMemsetAsync(hb.err, 0, sizeof(int), b->stream));
+    // bin the initial atoms into the buffer of step 0
+    double *d_pos = nullptr, *d_vel = nullptr;
+    const size_t nb = sizeof(double) * 3 * (size_t)std::max<int64_t>(hb.n_atoms, 1);
+    CU(cudaMalloc(&d_pos, nb));
+    if (b->has_vel && cudaMalloc(&d_vel, nb) != cudaSuccess) {
+        cudaFree(d_pos);
+        return DSEA_ERR_OOM;
+    }
+    int rc = DSEA_OK;
+    if (hb.n_atoms > 0) {
+        cudaMemcpyAsync(d_pos, b->pos0.data(), sizeof(double) * 3 * hb.n_atoms, cudaMemcpyHostToDevice,
+                        b->stream);
+        if (d_vel)
+            cudaMemcpyAsync(d_vel, b->vel0.data(), sizeof(double) * 3 * hb.n_atoms,
+                            cudaMemcpyHostToDevice, b->stream);
+    }
+    rc = upload_desc(b);
+    if (!rc) rc = map_cuda(dsea::launch_bin(hb, b->db, d_pos, d_vel, b->stream));
+    if (!rc) rc = check_device_error(b);
+    cudaFree(d_pos);
+    if (d_vel) cudaFree(d_vel);
+    if (rc) return rc;
+    b->pos0.clear();
+    b->pos0.shrink_to_fit();
+    b->vel0.clear();
+    b->vel0.shrink_to_fit();
+    b->registered = true;
+    return DSEA_OK;
+}
+
+int dsea_advance(dsea_box *b, int64_t n_steps)
+{
+    if (!b || n_steps < 0) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    if (b->latched) return b->latched;
+    return advance_impl(b, n_steps);
+}
+
+int dsea_sync(dsea_box *b)
+{
+    if (!b) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    return check_device_error(b);
+}
+
+int dsea_read_positions(dsea_box *b, double *out, int64_t n)
+{
+    int rc = read_array(b, out, n);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, b->hb.out_r, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return DSEA_OK;
+}
+
+int dsea_read_velocities(dsea_box *b, double *out, int64_t n)
+{
+    int rc = read_array(b, out, n);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, b->hb.out_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return DSEA_OK;
+}
+
+int dsea_read_forces(dsea_box *b, double *out, int64_t n)
+{
+    int rc = read_array(b, out, n);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, b->hb.out_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    return DSEA_OK;
+}
+
+int dsea_read_observables(dsea_box *b, dsea_observables *out)
+{
+    if (!b || !out) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    int rc = ensure_outputs(b);
+    if (rc) return rc;
+    out->step = b->hb.step;
+    out->U = b->obs3[0];
+    out->W = b->obs3[1];
+    out->KE = b->obs3[2];
+    return DSEA_OK;
+}
+
+int dsea_box_get_info(const dsea_box *b, dsea_box_info *o)
+{
+    if (!b || !o) return DSEA_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    const BoxDev &hb = b->hb;
+    o->n_atoms = hb.n_atoms;
+    o->step = hb.step;
+    if (!b->registered) return DSEA_OK;
+    o->n_slices = hb.n_slices;
+    o->cells_per_slice_x = hb.cps;
+    for (int d = 0; d < 3; ++d) {
+        o->cells[d] = hb.nc[d];
+        o->cell_edge[d] = hb.lc[d];
+    }
+    o->tile_y = hb.tile_y;
+    o->tile_z = hb.tile_z;
+    o->units_per_step = hb.n_slices * hb.units_per_slice;
+    o->cell_capacity = hb.cap;
+    o->precision = hb.precision;
+    o->schedule = b->params.schedule;
+    o->device_bytes = b->device_bytes;
+    return DSEA_OK;
+}
+
+int dsea_box_destroy(dsea_box *b)
+{
+    if (!b) return DSEA_ERR_INVALID_ARG;
+    if (b->registered) cudaStreamSynchronize(b->stream);
+    dev_free_all(b);
+    delete b;
+    return DSEA_OK;
+}
+
+int dsea_debug_set(dsea_box *b, int key, int64_t value)
+{
+    if (!b || !b->registered) return DSEA_ERR_INVALID_ARG;
+    switch (key) {
+    case DSEA_DEBUG_WITHHOLD_SLICE: b->hb.withhold_slice = (int)value; return DSEA_OK;
+    case DSEA_DEBUG_WAIT_LIMIT_NS:
+        if (value <= 0) return DSEA_ERR_INVALID_ARG;
+        b->hb.wait_limit_ns = value;
+        return DSEA_OK;
+    default: return DSEA_ERR_INVALID_ARG;
+    }
+}
+
+// ---- batches ----------------------------------------------------------------
+
+int dsea_batch_create(dsea_box *const *boxes, int n, dsea_batch **out)
+{
+    if (!boxes || n <= 0 || !out) return DSEA_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        if (!boxes[k] || !boxes[k]->registered) return DSEA_ERR_STATE;
+        if (boxes[k]->stream != boxes[0]->stream || boxes[k]->device != boxes[0]->device ||
+            boxes[k]->hb.precision != boxes[0]->hb.precision)
+            return DSEA_ERR_INVALID_ARG;
+        for (int q = 0; q < k; ++q)
+            if (boxes[q] == boxes[k]) return DSEA_ERR_INVALID_ARG;
+    }
+    dsea_batch *bt = new (std::nothrow) dsea_batch();
+    if (!bt) return DSEA_ERR_OOM;
+    bt->boxes.assign(boxes, boxes + n);
+    bt->stream = boxes[0]->stream;
+    bt->precision = boxes[0]->hb.precision;
+    if (cudaEventCreateWithFlags(&bt->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+        dsea::multi_reserve(bt->mp, n, 1024) != DSEA_OK) {
+        cudaGetLastError();
+        dsea_batch_destroy(bt);
+        return DSEA_ERR_OOM;
+    }
+    *out = bt;
+    return DSEA_OK;
+}
+
+int dsea_batch_advance(dsea_batch *bt, const int64_t *steps)
+{
+    if (!bt || !steps) return DSEA_ERR_INVALID_ARG;
+    const int n = (int)bt->boxes.size();
+    int64_t smax = 0;
+    for (int k = 0; k < n; ++k) {
+        if (steps[k] < 0) return DSEA_ERR_INVALID_ARG;
+        if (bt->boxes[k]->latched) return bt->boxes[k]->latched;
+        smax = std::max(smax, steps[k]);
+    }
+    if (smax == 0) return DSEA_OK;
+    if (smax > ((int64_t)1 << 30)) return DSEA_ERR_INVALID_ARG;
+    CU(cudaEventSynchronize(bt->done_ev));   // the previous replay has read the pinned plan
+    if (smax + 1 > bt->mp.cap_steps) {
+        for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);   // they hold old buffers
+        bt->graphs.clear();
+        int rc = dsea::multi_reserve(bt->mp, n, smax);
+        if (rc) return rc;
+    }
+    int rc = dsea::multi_prepare(bt->mp, bt->boxes.data(), steps, n);
+    if (rc) return rc;
+    std::vector<int64_t> key(2 * n + 1);
+    for (int k = 0; k < n; ++k) {
+        key[k] = bt->mp.order[k];
+        key[n + k] = steps[bt->mp.order[k]];
+    }
+    key[2 * n] = (int64_t)bt->mp.smem;
+    auto it = bt->graphs.find(key);
+    if (it == bt->graphs.end()) {
+        cudaStream_t st = bt->stream;
+        bool own = false;
+        if (st == nullptr) {   // the legacy stream cannot be captured: capture on a side stream
+            CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own = true;
+        }
+        // occupancy queries set kernel attributes: do them before capturing
+        dsea::ring_ctas_per_sm(bt->precision, bt->mp.smem);
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int erc = dsea::multi_enqueue(bt->mp, bt->boxes.data(), st);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (own) cudaStreamDestroy(st);
+        if (erc) {
+            if (g) cudaGraphDestroy(g);
+            return erc;
+        }
+        if (e != cudaSuccess) return map_cuda(e);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return map_cuda(e);
+        it = bt->graphs.emplace(key, ex).first;
+    }
+    CU(cudaGraphLaunch(it->second, bt->stream));
+    CU(cudaEventRecord(bt->done_ev, bt->stream));
+    dsea::multi_commit(bt->boxes.data(), steps, n);
+    return DSEA_OK;
+}
+
+int dsea_batch_destroy(dsea_batch *bt)
+{
+    if (!bt) return DSEA_ERR_INVALID_ARG;
+    if (bt->done_ev) {
+        cudaEventSynchronize(bt->done_ev);
+        cudaEventDestroy(bt->done_ev);
+    }
+    for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);
+    dsea::multi_free(bt->mp);
+    delete bt;
+    return DSEA_OK;
+}
+
+// ---- autotuner ----------------------------------------------------------------
+
+int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
+{
+    if (!b || trial_steps <= 0) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    int rc = check_device_error(b);
+    if (rc) return rc;
+    BoxDev &hb = b->hb;
+    const TuneKey key{hb.nc[0], hb.nc[1], hb.nc[2], hb.cps, hb.cap, hb.precision};
+    std::pair<int, int> best{hb.tile_y, hb.tile_z};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        // snapshot the current state buffer so the trials leave the box unchanged
+        const int p = (int)(hb.step & 1);
+        const int64_t step0 = hb.step;
+        const int sync0 = hb.w_is_sync;
+        const size_t b_cnt = sizeof(unsigned long long) * hb.n_cells, b_id = sizeof(int) * hb.n_slots,
+                     b_r = sizeof(double) * 3 * hb.n_slots, b_q = sizeof(float4) * hb.n_slots;
+        void *s_cnt = nullptr, *s_id = nullptr, *s_r = nullptr, *s_v = nullptr, *s_q = nullptr;
+        bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess && cudaMalloc(&s_id, b_id) == cudaSuccess &&
+                  cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_r) == cudaSuccess &&
+                  (hb.precision != DSEA_MIXED || cudaMalloc(&s_q, b_q) == cudaSuccess);
+        auto release = [&]() {
+            cudaFree(s_cnt); cudaFree(s_id); cudaFree(s_r); cudaFree(s_v);
+            if (s_q) cudaFree(s_q);
+        };
+        if (!ok) {
+            cudaGetLastError();
+            release();
+            return DSEA_ERR_OOM;
+        }
+        auto copy = [&](bool save) -> cudaError_t {
+            auto c = [&](void *snap, void *live, size_t bytes) {
+                return save ? cudaMemcpyAsync(snap, live, bytes, cudaMemcpyDeviceToDevice, b->stream)
+                            : cudaMemcpyAsync(live, snap, bytes, cudaMemcpyDeviceToDevice, b->stream);
+            };
+            cudaError_t e = c(s_cnt, hb.cnt[p], b_cnt);
+            if (e == cudaSuccess) e = c(s_id, hb.id[p], b_id);
+            if (e == cudaSuccess) e = c(s_r, hb.r[p], b_r);
+            if (e == cudaSuccess) e = c(s_v, hb.v[p], b_r);
+            if (e == cudaSuccess && s_q) e = c(s_q, hb.q[p], b_q);
+            if (e == cudaSuccess && !save)   // stale counts of the other buffer must not match
+                e = cudaMemsetAsync(hb.cnt[p ^ 1], 0, b_cnt, b->stream);
+            return e;
+        };
+        if (copy(true) != cudaSuccess) {
+            release();
+            return DSEA_ERR_CUDA;
+        }
+        static const int cand[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        const int sched = b->params.schedule;
+        const BoxDev saved = hb;
+        for (const auto &c : cand) {
+            BoxDev trial = saved;
+            if (!apply_tile(trial, b->mean_cap, c[0], c[1])) continue;
+            if (trial.tile_y != c[0] || trial.tile_z != c[1]) continue;   // clipped duplicate
+            hb = trial;
+            b->params.schedule = DSEA_SCHED_RING;
+            rc = advance_impl(b, 1);   // warm-up
+            if (!rc) {
+                cudaEventRecord(e0, b->stream);
+                rc = advance_impl(b, trial_steps);
+                cudaEventRecord(e1, b->stream);
+            }
+            if (!rc) rc = check_device_error(b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            hb.step = step0;
+            hb.w_is_sync = sync0;
+            copy(false);
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = {trial.tile_y, trial.tile_z};
+            }
+        }
+        b->params.schedule = sched;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamSynchronize(b->stream);
+        release();
+        hb = saved;
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    apply_tile(hb, b->mean_cap, best.first, best.second);
+    b->params.tile_y = hb.tile_y;
+    b->params.tile_z = hb.tile_z;
+    b->outputs_valid = false;
+    if (chosen) *chosen = b->params;
+    return DSEA_OK;
+}
+
+// ---- schedule introspection ---------------------------------------------------
+
+int dsea_ring_order(int n_slices, int units_per_slice, int64_t n_steps, int64_t start_step,
+                    int32_t *out_slice, int32_t *out_step)
+{
+    if (n_slices < 3 || units_per_slice < 1 || n_steps < 0 || start_step < 0 || !out_slice || !out_step)
+        return DSEA_ERR_INVALID_ARG;
+    const int64_t U = (int64_t)n_slices * units_per_slice;
+    for (int64_t t = 0; t < n_steps * U; ++t) {
+        const int64_t s = t / U, m = t - s * U;
+        const int jj = (int)(m / units_per_slice);
+        out_slice[t] = dsea::ring_slice(jj, start_step + s, n_slices);
+        out_step[t] = (int32_t)s;
+    }
+    return DSEA_OK;
+}
+
+}  // extern "C"
+
+// ---- shared host machinery (used by batches and the server) -------------------
+
+namespace dsea {
+
+void multi_free(MultiPlan &mp)
+{
+    if (mp.d_boxes) cudaFree(mp.d_boxes);
+    if (mp.h_boxes) cudaFreeHost(mp.h_boxes);
+    if (mp.d_cum) cudaFree(mp.d_cum);
+    if (mp.h_cum) cudaFreeHost(mp.h_cum);
+    if (mp.d_step_base) cudaFree(mp.d_step_base);
+    if (mp.h_step_base) cudaFreeHost(mp.h_step_base);
+    if (mp.d_active) cudaFree(mp.d_active);
+    if (mp.h_active) cudaFreeHost(mp.h_active);
+    if (mp.d_ticket) cudaFree(mp.d_ticket);
+    if (mp.d_err) cudaFree(mp.d_err);
+    mp = MultiPlan();
+}
+
+int multi_reserve(MultiPlan &mp, int n, int64_t smax)
+{
+    if (n <= mp.cap_boxes && smax + 1 <= mp.cap_steps) return DSEA_OK;
+    const int nb = std::max(n, mp.cap_boxes);
+    const int64_t ns = std::max<int64_t>(smax + 1, mp.cap_steps);
+    multi_free(mp);
+    bool ok = cudaMalloc(&mp.d_boxes, sizeof(BoxDev) * nb) == cudaSuccess &&
+              cudaMallocHost(&mp.h_boxes, sizeof(BoxDev) * nb) == cudaSuccess &&
+              cudaMalloc(&mp.d_cum, sizeof(int64_t) * (nb + 1)) == cudaSuccess &&
+              cudaMallocHost(&mp.h_cum, sizeof(int64_t) * (nb + 1)) == cudaSuccess &&
+              cudaMalloc(&mp.d_step_base, sizeof(int64_t) * ns) == cudaSuccess &&
+              cudaMallocHost(&mp.h_step_base, sizeof(int64_t) * ns) == cudaSuccess &&
+              cudaMalloc(&mp.d_active, sizeof(int) * ns) == cudaSuccess &&
+              cudaMallocHost(&mp.h_active, sizeof(int) * ns) == cudaSuccess &&
+              cudaMalloc(&mp.d_ticket, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&mp.d_err, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        multi_free(mp);
+        return DSEA_ERR_OOM;
+    }
+    mp.cap_boxes = nb;
+    mp.cap_steps = ns;
+    return DSEA_OK;
+}
+
+int multi_prepare(MultiPlan &mp, dsea_box *const *boxes, const int64_t *steps, int n)
+{
+    int64_t smax = 0;
+    for (int k = 0; k < n; ++k) smax = std::max(smax, steps[k]);
+    int rc = multi_reserve(mp, n, smax);
+    if (rc) return rc;
+    // boxes with more steps first: the active boxes of each level are a prefix
+    mp.order.resize(n);
+    for (int k = 0; k < n; ++k) mp.order[k] = k;
+    std::stable_sort(mp.order.begin(), mp.order.end(),
+                     [&](int a, int c) { return steps[a] > steps[c]; });
+    mp.smem = 0;
+    mp.precision = n > 0 ? boxes[0]->hb.precision : 0;
+    mp.h_cum[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        dsea_box *b = boxes[mp.order[k]];
+        if (b->hb.precision != mp.precision) return DSEA_ERR_INVALID_ARG;
+        mp.h_boxes[k] = b->hb;
+        mp.h_cum[k + 1] = mp.h_cum[k] + (int64_t)b->hb.n_slices * b->hb.units_per_slice;
+        mp.smem = std::max(mp.smem, unit_smem_bytes(b->hb.precision, b->hb.staged_cells, b->hb.smem_atoms));
+    }
+    int64_t total = 0;
+    int act = n;
+    for (int64_t s = 0; s < smax; ++s) {
+        while (act > 0 && steps[mp.order[act - 1]] <= s) --act;
+        mp.h_active[s] = act;
+        mp.h_step_base[s] = total;
+        total += mp.h_cum[act];
+    }
+    mp.h_step_base[smax] = total;
+    mp.n = n;
+    mp.smax = smax;
+    mp.total = total;
+    return DSEA_OK;
+}
+
+int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t st)
+{
+    if (mp.total == 0) return DSEA_OK;
+    const int n = mp.n;
+    CU(cudaMemcpyAsync(mp.d_boxes, mp.h_boxes, sizeof(BoxDev) * n, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(mp.d_cum, mp.h_cum, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(mp.d_step_base, mp.h_step_base, sizeof(int64_t) * (mp.smax + 1),
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(mp.d_active, mp.h_active, sizeof(int) * mp.smax, cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < n; ++k)
+        CU(cudaMemsetAsync(boxes[k]->hb.done, 0, sizeof(unsigned) * boxes[k]->hb.n_slices, st));
+    CU(cudaMemsetAsync(mp.d_ticket, 0, sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(mp.d_err, 0, sizeof(int), st));
+    RingPlan plan{};
+    plan.boxes = mp.d_boxes;
+    plan.step_base = mp.d_step_base;
+    plan.cum_units = mp.d_cum;
+    plan.active = mp.d_active;
+    plan.n_boxes = n;
+    plan.n_steps = (int)mp.smax;
+    plan.total = mp.total;
+    plan.ticket = mp.d_ticket;
+    plan.err = mp.d_err;
+    int ctas = num_sms() * std::max(1, ring_ctas_per_sm(mp.precision, mp.smem));
+    if ((int64_t)ctas > mp.total) ctas = (int)mp.total;
+    CU(launch_ring(plan, mp.precision, mp.smem, ctas, st));
+    return DSEA_OK;
+}
+
+void multi_commit(dsea_box *const *boxes, const int64_t *steps, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        if (steps[k] <= 0) continue;
+        boxes[k]->hb.step += steps[k];
+        boxes[k]->hb.w_is_sync = 0;
+        boxes[k]->outputs_valid = false;
+    }
+}
+
+int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, size_t *bytes)
+{
+    if (!desc || !bytes) return DSEA_ERR_INVALID_ARG;
+    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0};
+    if (params) p = *params;
+    BoxDev hb{};
+    double mean_cap = 0;
+    int rc = setup_geometry(desc->n_slices, desc->box, desc->n_atoms, p, hb, mean_cap);
+    if (rc) return rc;
+    const size_t per_slot = sizeof(int) + 6 * sizeof(double) + (p.precision == DSEA_MIXED ? sizeof(float4) : 0);
+    size_t b = 2 * ((size_t)hb.n_cells * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
+    b += (size_t)hb.n_cells * 3 * sizeof(double);              // unit partials
+    b += (size_t)desc->n_atoms * 9 * sizeof(double);           // read-back arrays
+    b += 64 * 1024;                                            // descriptors, counters, plans
+    *bytes = b;
+    return DSEA_OK;
+}
+
+int read_state(dsea_box *b, double *pos, double *vel, dsea_observables *obs)
+{
+    if (!b || !b->registered) return DSEA_ERR_STATE;
+    int rc = ensure_outputs(b);
+    if (rc) return rc;
+    const size_t nb = sizeof(double) * 3 * (size_t)b->hb.n_atoms;
+    if (pos) CU(cudaMemcpyAsync(pos, b->hb.out_r, nb, cudaMemcpyDeviceToHost, b->stream));
+    if (vel) CU(cudaMemcpyAsync(vel, b->hb.out_v, nb, cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    if (obs) {
+        obs->step = b->hb.step;
+        obs->U = b->obs3[0];
+        obs->W = b->obs3[1];
+        obs->KE = b->obs3[2];
+    }
+    return DSEA_OK;
+}
+
+}  // namespace dsea

@@ -1,0 +1,79 @@
+// dsea_host.h -- host-side objects shared by the C-ABI translation units
+// (dsea_api.cu, dsea_server.cu); not part of the ABI.
+#pragma once
+
+#include "dsea.h"
+#include "dsea_internal.h"
+
+#include <map>
+#include <vector>
+
+struct dsea_box {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    dsea_allocator alloc{};
+    bool has_alloc = false;
+    int n_slices_req = 0;
+    double L[3] = {0, 0, 0};
+    std::vector<double> pos0, vel0;   // host copies until the kernel is registered
+    bool has_vel = false;
+    bool registered = false;
+    dsea_params params{};
+    double mean_cap = 0;              // expected atoms per cell used for stage sizing
+    dsea::BoxDev hb{};
+    dsea::BoxDev *db = nullptr;
+    std::vector<void *> allocs;
+    size_t device_bytes = 0;
+    // ring plan buffers of single-box launches
+    int64_t *d_step_base = nullptr;
+    int64_t step_base_cap = 0;
+    int64_t *d_cum = nullptr;
+    int *d_active = nullptr;
+    unsigned long long *d_ticket = nullptr;
+    int *d_launch_err = nullptr;
+    double *d_obs3 = nullptr;
+    double obs3[3] = {0, 0, 0};
+    bool outputs_valid = false;
+    int latched = DSEA_OK;            // first device error seen
+};
+
+namespace dsea {
+
+// Reusable buffers of a persistent launch over several boxes.  The host half
+// is pinned so that a captured graph can re-read it on every replay.
+struct MultiPlan {
+    int cap_boxes = 0;
+    int64_t cap_steps = 0;
+    BoxDev *d_boxes = nullptr, *h_boxes = nullptr;
+    int64_t *d_cum = nullptr, *h_cum = nullptr;
+    int64_t *d_step_base = nullptr, *h_step_base = nullptr;
+    int *d_active = nullptr, *h_active = nullptr;
+    unsigned long long *d_ticket = nullptr;
+    int *d_err = nullptr;
+    // filled by multi_prepare
+    int n = 0;
+    int64_t smax = 0, total = 0;
+    size_t smem = 0;
+    int precision = 0;
+    std::vector<int> order;
+};
+
+// Make room for n boxes and smax steps (frees and reallocates as needed).
+int multi_reserve(MultiPlan &mp, int n, int64_t smax);
+// Host half of a launch advancing boxes[k] by steps[k]; the pinned buffers
+// must not be in use by an earlier launch.
+int multi_prepare(MultiPlan &mp, dsea_box *const *boxes, const int64_t *steps, int n);
+// Enqueue the plan upload, the counter resets and the ring launch.
+int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t stream);
+// After the launch has been enqueued: advance the host step counters.
+void multi_commit(dsea_box *const *boxes, const int64_t *steps, int n);
+void multi_free(MultiPlan &mp);
+
+// Device bytes a box of this description would hold once registered.
+int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, size_t *bytes);
+
+// Force pass + read-back of positions, velocities (and observables) into host
+// arrays (any may be NULL); synchronises the box.
+int read_state(dsea_box *b, double *pos, double *vel, dsea_observables *obs);
+
+}  // namespace dsea

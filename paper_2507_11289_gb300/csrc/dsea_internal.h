@@ -1,0 +1,112 @@
+// dsea_internal.h -- device-side box descriptor and the launch entry points
+// shared by the CUDA translation units of the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dsea {
+
+constexpr int kThreads = 256;            // threads per work-unit CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxStagedCells = 2048;    // staged neighbourhood cells per unit (upper bound)
+
+// Device error word values (first error wins).
+enum : int {
+    kErrNone = 0,
+    kErrCapacity = 1,   // a cell or the shared-memory stage overflowed
+    kErrMigration = 2,  // an atom left slices j-1..j+1 in one step
+    kErrTimeout = 3,    // a bounded dependency wait expired
+};
+
+// One box as the kernels see it.  Slot layout: the state of a step lives in
+// one of two buffers (step parity).  Cell c owns slots [c*cap, c*cap + cap);
+// per-slot arrays are SoA (component k of slot t at k*n_slots + t).
+struct BoxDev {
+    // geometry (Sec. 4: cells of edge >= rc, slices of cps cell layers in x)
+    double L[3];
+    double lc[3];
+    double inv_lc[3];
+    float lcf[3];
+    int nc[3];
+    int n_slices;
+    int cps;
+    // work units: tile_y x tile_z home cells (all cps layers of one slice)
+    int tile_y, tile_z, tiles_y, tiles_z, units_per_slice;
+    int cap;
+    int precision;
+    int staged_cells;  // max staged cells of a unit
+    int smem_atoms;    // staged atoms the unit's shared memory holds
+    int64_t n_cells;
+    int64_t n_slots;   // n_cells * cap
+    int64_t n_atoms;
+    // pair law (Algorithm 1)
+    double rc2, ushift, dt;
+    float rc2f, ushiftf;
+    // state, two step-parity buffers
+    unsigned long long *cnt[2];  // per cell: (tag << 32) | count, tag = step + 1
+    int *id[2];
+    double *r[2];   // absolute positions, 3 * n_slots
+    double *v[2];   // velocities (half-step after the first step), 3 * n_slots
+    float4 *q[2];   // mixed: cell-centred FP32 coordinates, atom id bits in .w
+    // per advance
+    int64_t step;   // absolute step of the current state
+    int w_is_sync;  // 1 until the first step: v holds v(t0), not v(t-dt/2)
+    int withhold_slice;   // testing hook: this slice never reports completion (-1 = off)
+    unsigned *done;       // [n_slices] completed units of the running launch
+    int *err;             // device error word
+    double *unit_obs;     // [units_per_step * 3] (U, W, KE) partials of a force pass
+    double *out_r, *out_v, *out_f;  // readback by atom id, 3 * n_atoms each
+    long long wait_limit_ns;        // bounded-wait limit of the ring
+};
+
+// Slice processed by the jj-th slice group of level s_abs in the ring's
+// dispatch order: each level starts two slices after the previous one.
+__host__ __device__ inline int ring_slice(int jj, long long s_abs, int n_slices)
+{
+    return (int)((jj + 2 * (s_abs % n_slices)) % n_slices);
+}
+
+// Dynamic shared memory bytes a unit of this box needs.
+size_t unit_smem_bytes(int precision, int staged_cells, int smem_atoms);
+
+// Largest dynamic shared memory a unit may use on this device.
+size_t max_unit_smem_bytes();
+
+// Bin atoms (device AoS pos/vel, atom-ID order) into the buffer of `box.step`.
+cudaError_t launch_bin(const BoxDev &host_box, const BoxDev *dev_box, const double *pos,
+                       const double *vel, cudaStream_t stream);
+
+// One step of all units of one box, one launch (no device waits).
+cudaError_t launch_step(const BoxDev &host_box, const BoxDev *dev_box, int64_t s_abs,
+                        int first_step, cudaStream_t stream);
+
+// Force pass at the current state: forces, synchronised velocities and
+// positions scattered by atom id, plus (U, W, KE) partials per unit.
+cudaError_t launch_force_pass(const BoxDev &host_box, const BoxDev *dev_box, cudaStream_t stream);
+
+// Deterministic fixed-order sum of the unit partials into out3 (device).
+cudaError_t launch_obs_reduce(const double *unit_obs, int n_units, double *out3,
+                              cudaStream_t stream);
+
+// The persistent ring over one or more boxes (same precision).
+struct RingPlan {
+    const BoxDev *boxes;        // device array [n_boxes]
+    const int64_t *step_base;   // [n_steps + 1] first ticket of each relative step
+    const int64_t *cum_units;   // [n_boxes + 1] prefix sums of units per step
+    const int *active;          // [n_steps] boxes active at each relative step
+    int n_boxes;
+    int n_steps;                // relative steps in this launch (max over boxes)
+    int64_t total;              // tickets
+    unsigned long long *ticket; // dispenser
+    int *err;                   // launch-wide error word
+};
+cudaError_t launch_ring(const RingPlan &plan, int precision, size_t smem_bytes, int ctas,
+                        cudaStream_t stream);
+
+// Occupancy of the ring kernel (CTAs per SM) for a shared-memory size.
+int ring_ctas_per_sm(int precision, size_t smem_bytes);
+
+}  // namespace dsea

@@ -1,0 +1,770 @@
+// dsea_kernels.cu -- sm_103a kernels of the slice-streamed LJ NVE step.
+//
+// One work unit = all home cells of one slice (its cps cell layers along x)
+// within a tile_y x tile_z block of cells in (y, z).  A unit
+//   1. stages the counts of its neighbourhood cells (home cells plus one cell
+//      layer around them, periodic) and an exclusive scan of them,
+//   2. stages the atoms of those cells into shared memory, each cell sorted
+//      by atom id (so every sum below runs in an order fixed by the state
+//      alone: the same whatever the unit shape, launch form or batch),
+//   3. computes, warp per home cell, the force on each home atom from the 27
+//      neighbour cells (Algorithm 1's first loop, Sec. 4.1 "md_v3a"),
+//   4. (INTEGRATE) kicks and drifts each home atom (Algorithm 1's second and
+//      third loops, "md_v3aa" / "md_v3b") and appends it to the cell it
+//      moved to in the next-step buffer, which may belong to slice j-1, j or
+//      j+1 (O_out = 1, Sec. 4); warp-aggregated atomics reserve the slots,
+//   5. (OBS) reduces U, W and KE of its home atoms in FP64 ("stat_collect").
+//
+// The FP64 form evaluates pairs on absolute positions; the mixed form on
+// FP32 coordinates relative to each atom's cell centre, with FP64 kept for
+// absolute positions, the position update and every reduction.
+#include "dsea_internal.h"
+
+#include <cstdio>
+
+namespace dsea {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void set_error(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int *p)
+{
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared-memory carve-up of one unit.
+struct Layout {
+    size_t cnt, start, gcell, atoms, id, slot, scr, red, total;
+};
+
+__host__ __device__ inline Layout make_layout(int precision, int staged_cells, int smem_atoms)
+{
+    Layout L;
+    size_t o = 0;
+    L.cnt = o;   o += sizeof(int) * staged_cells;
+    L.start = o; o += sizeof(int) * (staged_cells + 1);
+    L.gcell = o; o += sizeof(int) * staged_cells;
+    o = align16(o);
+    L.atoms = o;
+    if (precision == 1) {
+        o += sizeof(float4) * smem_atoms;       // x, y, z, id bits
+        L.id = 0;
+    } else {
+        o += 3 * sizeof(double) * smem_atoms;   // x[], y[], z[]
+        L.id = o;
+        o += sizeof(int) * smem_atoms;
+    }
+    L.slot = o; o += sizeof(int) * smem_atoms;
+    o = align16(o);
+    L.scr = o;  o += sizeof(double) * kThreads * 5;
+    L.red = o;  o += sizeof(double) * kWarps * 3;
+    L.total = align16(o);
+    return L;
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n)
+{
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Force accumulators of one lane.
+template <typename T>
+struct Acc {
+    T fx, fy, fz, u, w;
+};
+
+// One candidate pair in FP32 (mixed form).  The lane's home atom, already
+// moved into the neighbour cell's frame, is (xs, ys, zs).
+template <bool OBS>
+__device__ __forceinline__ void pair_f32(float xs, float ys, float zs, const float4 pj, float rc2,
+                                         float ushift, Acc<float> &a)
+{
+    const float dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const bool in = (r2 <= rc2) & (r2 > 0.f);
+    const float r2i = rcp_approx(in ? r2 : 1.f);
+    const float r6i = r2i * r2i * r2i;
+    float fs = r2i * r6i * fmaf(48.f, r6i, -24.f);   // F_abs = 24 (2 r^-12 - r^-6) / r^2
+    fs = in ? fs : 0.f;
+    a.fx = fmaf(dx, fs, a.fx);
+    a.fy = fmaf(dy, fs, a.fy);
+    a.fz = fmaf(dz, fs, a.fz);
+    if (OBS) {
+        const float u = fmaf(4.f * r6i, r6i - 1.f, ushift);  // 4 (r^-12 - r^-6) + U_shift
+        a.u += in ? u : 0.f;
+        a.w = fmaf(r2, fs, a.w);                              // r_ij . F_ij
+    }
+}
+
+// One candidate pair in FP64 on absolute (periodically shifted) positions.
+template <bool OBS>
+__device__ __forceinline__ void pair_f64(double xi, double yi, double zi, double xj, double yj,
+                                         double zj, double rc2, double ushift, Acc<double> &a)
+{
+    const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 <= rc2 && r2 > 0.0) {
+        const double r2i = 1.0 / r2;
+        const double r6i = r2i * r2i * r2i;
+        const double fs = 24.0 * (2.0 * r6i * r6i - r6i) * r2i;
+        a.fx += dx * fs;
+        a.fy += dy * fs;
+        a.fz += dz * fs;
+        if (OBS) {
+            a.u += 4.0 * (r6i * r6i - r6i) + ushift;
+            a.w += r2 * fs;
+        }
+    }
+}
+
+// Reserve `1` slot per lane in cell `dest` of the next-step buffer; lanes
+// with the same destination share one compare-and-swap (warp aggregation).
+// Returns the slot index within the cell, or -1 for inactive lanes.
+__device__ __forceinline__ int reserve_slot(unsigned long long *cnt, long long dest, bool active,
+                                            unsigned tag, int lane, int *err)
+{
+    const long long key = active ? dest : -1 - (long long)lane;
+    const unsigned grp = __match_any_sync(kFull, key);
+    const int leader = __ffs(grp) - 1;
+    const int rank = __popc(grp & ((1u << lane) - 1u));
+    int base = 0;
+    if (active && lane == leader) {
+        const unsigned gsize = __popc(grp);
+        unsigned long long *p = cnt + dest;
+        unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(p);
+        int tries = 0;
+        while (true) {
+            const unsigned c = ((unsigned)(old >> 32) == tag) ? (unsigned)old : 0u;
+            const unsigned long long nv = ((unsigned long long)tag << 32) | (unsigned long long)(c + gsize);
+            const unsigned long long prev = atomicCAS(p, old, nv);
+            if (prev == old) {
+                base = (int)c;
+                break;
+            }
+            old = prev;
+            if (++tries > (1 << 20)) {   // lock-free, so this never triggers in practice
+                set_error(err, kErrTimeout);
+                base = 1 << 29;
+                break;
+            }
+        }
+    }
+    base = __shfl_sync(kFull, base, leader);
+    return active ? base + rank : -1;
+}
+
+// Write one atom into slot `slot` of buffer `pn`.
+template <int PREC>
+__device__ __forceinline__ void store_atom(const BoxDev &B, int pn, long long slot, int aid,
+                                           long long cell, double x, double y, double z,
+                                           double vx, double vy, double vz, int cx, int cy, int cz)
+{
+    const long long S = B.n_slots;
+    B.id[pn][slot] = aid;
+    B.r[pn][slot] = x;
+    B.r[pn][S + slot] = y;
+    B.r[pn][2 * S + slot] = z;
+    B.v[pn][slot] = vx;
+    B.v[pn][S + slot] = vy;
+    B.v[pn][2 * S + slot] = vz;
+    if (PREC == 1) {
+        // FP32 coordinates relative to the centre of the atom's cell
+        const float qx = (float)(x - ((double)cx + 0.5) * B.lc[0]);
+        const float qy = (float)(y - ((double)cy + 0.5) * B.lc[1]);
+        const float qz = (float)(z - ((double)cz + 0.5) * B.lc[2]);
+        B.q[pn][slot] = make_float4(qx, qy, qz, __int_as_float(aid));
+    }
+    (void)cell;
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L)
+{
+    if (x >= L) x -= L;
+    else if (x < 0.0) x += L;
+    if (x >= L) x -= L;        // x = -tiny rounds to L: fold back to 0
+    if (x < 0.0) x = 0.0;
+    return x;
+}
+
+__device__ __forceinline__ int cell_of(double x, double inv_lc, int n)
+{
+    int c = (int)(x * inv_lc);
+    return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// The work unit (see file header).  s_abs: absolute step of the input state.
+template <int PREC, bool INTEGRATE, bool OBS>
+__device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool first_step,
+                         int unit_id, char *smem)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int p = (int)(s_abs & 1);
+    const unsigned tag = (unsigned)(s_abs + 1);
+    const Layout Ly = make_layout(PREC, B.staged_cells, B.smem_atoms);
+    int *s_cnt = reinterpret_cast<int *>(smem + Ly.cnt);
+    int *s_start = reinterpret_cast<int *>(smem + Ly.start);
+    int *s_gcell = reinterpret_cast<int *>(smem + Ly.gcell);
+    int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
+    double *s_scr = reinterpret_cast<double *>(smem + Ly.scr);
+    double *s_red = reinterpret_cast<double *>(smem + Ly.red);
+    float4 *s_q = reinterpret_cast<float4 *>(smem + Ly.atoms);
+    double *s_x = reinterpret_cast<double *>(smem + Ly.atoms);
+    double *s_y = s_x + B.smem_atoms;
+    double *s_z = s_y + B.smem_atoms;
+    int *s_id = reinterpret_cast<int *>(smem + Ly.id);
+
+    // unit geometry
+    const int tyi = tile / B.tiles_z, tzi = tile - (tile / B.tiles_z) * B.tiles_z;
+    const int y0 = tyi * B.tile_y, z0 = tzi * B.tile_z;
+    const int ny = min(B.tile_y, B.nc[1] - y0), nz = min(B.tile_z, B.nc[2] - z0);
+    const int x0 = j * B.cps, nx = B.cps;
+    const int EY = ny + 2, EZ = nz + 2;
+    const int n_staged = (nx + 2) * EY * EZ;
+
+    // 1. counts of the staged cells
+    for (int k = tid; k < n_staged; k += kThreads) {
+        const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
+        const int gx = wrap_index(x0 - 1 + lx, B.nc[0]);
+        const int gy = wrap_index(y0 - 1 + ly, B.nc[1]);
+        const int gz = wrap_index(z0 - 1 + lz, B.nc[2]);
+        const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
+        const unsigned long long w = __ldcg(B.cnt[p] + gc);
+        int c = ((unsigned)(w >> 32) == tag) ? (int)(unsigned)w : 0;
+        if (c > B.cap) {
+            set_error(B.err, kErrCapacity);
+            c = B.cap;
+        }
+        s_cnt[k] = c;
+        s_gcell[k] = gc;
+    }
+    __syncthreads();
+    // 2. exclusive scan (warp 0, contiguous chunks per lane)
+    if (warp == 0) {
+        const int per = (n_staged + 31) / 32;
+        const int b = lane * per, e = min(b + per, n_staged);
+        int sum = 0;
+        for (int k = b; k < e; ++k) sum += s_cnt[k];
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+        for (int k = b; k < e; ++k) {
+            s_start[k] = run;
+            run += s_cnt[k];
+        }
+        if (lane == 31) s_start[n_staged] = incl;
+    }
+    __syncthreads();
+    if (s_start[n_staged] > B.smem_atoms) {   // uniform across the CTA
+        if (tid == 0) set_error(B.err, kErrCapacity);
+        return;
+    }
+    // 3. stage atoms, each cell sorted by atom id (warp per cell)
+    const long long S = B.n_slots;
+    for (int k = warp; k < n_staged; k += kWarps) {
+        const int c = s_cnt[k];
+        if (c == 0) continue;
+        const long long base = (long long)s_gcell[k] * B.cap;
+        const int *ids = B.id[p] + base;
+        double shx = 0.0, shy = 0.0, shz = 0.0;
+        if (PREC == 0) {   // periodic image shift of this staged cell
+            const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
+            const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
+            shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
+            shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
+            shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
+        }
+        for (int a0 = 0; a0 < c; a0 += 32) {
+            const int a = a0 + lane;
+            const int myid = a < c ? __ldcg(ids + a) : 0x7fffffff;
+            int rank = 0;
+            for (int b0 = 0; b0 < c; b0 += 32) {
+                const int other = (b0 + lane < c) ? __ldcg(ids + b0 + lane) : 0x7fffffff;
+                const int lim = min(32, c - b0);
+                for (int t = 0; t < lim; ++t) rank += (__shfl_sync(kFull, other, t) < myid) ? 1 : 0;
+            }
+            if (a < c) {
+                const int dst = s_start[k] + rank;
+                const long long slot = base + a;
+                s_slot[dst] = (int)slot;
+                if (PREC == 1) {
+                    s_q[dst] = __ldcg(B.q[p] + slot);
+                } else {
+                    s_x[dst] = __ldcg(B.r[p] + slot) + shx;
+                    s_y[dst] = __ldcg(B.r[p] + S + slot) + shy;
+                    s_z[dst] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+                    s_id[dst] = myid;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 4. forces, warp per home cell; lanes = (home atom, candidate split)
+    double red_u = 0.0, red_w = 0.0, red_k = 0.0;
+    const int n_home = nx * ny * nz;
+    const int pn = p ^ 1;
+    const unsigned tag_next = tag + 1u;
+    const double dt = B.dt;
+    const double kick = first_step ? 0.5 * dt : dt;
+    for (int h = warp; h < n_home; h += kWarps) {
+        const int hx = h / (ny * nz), hr = h - hx * ny * nz, hy = hr / nz, hz = hr - hy * nz;
+        const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
+        const int n_i = s_cnt[kh];
+        const int hs = s_start[kh];
+        for (int ib = 0; ib < n_i; ib += 32) {
+            const int nin = min(32, n_i - ib);
+            const int ns = 32 / nin;
+            const int li = lane % nin, g = lane / nin;
+            const bool act = g < ns;
+            const int is = hs + ib + li;
+            Acc<float> a32 = {0.f, 0.f, 0.f, 0.f, 0.f};
+            Acc<double> a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (act) {
+                if (PREC == 1) {
+                    const float4 qi = s_q[is];
+                    for (int ox = -1; ox <= 1; ++ox)
+                        for (int oy = -1; oy <= 1; ++oy)
+                            for (int oz = -1; oz <= 1; ++oz) {
+                                const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+                                const int cs = s_start[kn], cn = s_cnt[kn];
+                                // home atom in the neighbour cell's centred frame
+                                const float xs = qi.x - (float)ox * B.lcf[0];
+                                const float ys = qi.y - (float)oy * B.lcf[1];
+                                const float zs = qi.z - (float)oz * B.lcf[2];
+                                for (int t = g; t < cn; t += ns)
+                                    pair_f32<OBS>(xs, ys, zs, s_q[cs + t], B.rc2f, B.ushiftf, a32);
+                            }
+                } else {
+                    const double xi = s_x[is], yi = s_y[is], zi = s_z[is];
+                    for (int ox = -1; ox <= 1; ++ox)
+                        for (int oy = -1; oy <= 1; ++oy)
+                            for (int oz = -1; oz <= 1; ++oz) {
+                                const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+                                const int cs = s_start[kn], cn = s_cnt[kn];
+                                for (int t = g; t < cn; t += ns)
+                                    pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t],
+                                                  B.rc2, B.ushift, a64);
+                            }
+                }
+            }
+            // combine the ns partial sums of each home atom in split order
+            double fx, fy, fz, uu, ww;
+            if (PREC == 1) {
+                fx = a32.fx; fy = a32.fy; fz = a32.fz; uu = a32.u; ww = a32.w;
+            } else {
+                fx = a64.fx; fy = a64.fy; fz = a64.fz; uu = a64.u; ww = a64.w;
+            }
+            if (ns > 1) {
+                double *scr = s_scr + warp * 32 * 5;
+                if (PREC == 1) {
+                    float *sf = reinterpret_cast<float *>(scr);
+                    sf[lane * 5 + 0] = a32.fx; sf[lane * 5 + 1] = a32.fy; sf[lane * 5 + 2] = a32.fz;
+                    sf[lane * 5 + 3] = a32.u;  sf[lane * 5 + 4] = a32.w;
+                    __syncwarp();
+                    if (g == 0) {
+                        float bx = a32.fx, by = a32.fy, bz = a32.fz, bu = a32.u, bw = a32.w;
+                        for (int gg = 1; gg < ns; ++gg) {
+                            const int o = (li + gg * nin) * 5;
+                            bx += sf[o]; by += sf[o + 1]; bz += sf[o + 2]; bu += sf[o + 3]; bw += sf[o + 4];
+                        }
+                        fx = bx; fy = by; fz = bz; uu = bu; ww = bw;
+                    }
+                } else {
+                    scr[lane * 5 + 0] = a64.fx; scr[lane * 5 + 1] = a64.fy; scr[lane * 5 + 2] = a64.fz;
+                    scr[lane * 5 + 3] = a64.u;  scr[lane * 5 + 4] = a64.w;
+                    __syncwarp();
+                    if (g == 0) {
+                        for (int gg = 1; gg < ns; ++gg) {
+                            const int o = (li + gg * nin) * 5;
+                            fx += scr[o]; fy += scr[o + 1]; fz += scr[o + 2]; uu += scr[o + 3]; ww += scr[o + 4];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // 5. kick, drift, rebin (lanes holding a home atom: lane < nin)
+            const bool own = lane < nin;
+            int aid = 0;
+            long long slot = 0;
+            double rx = 0, ry = 0, rz = 0, vx = 0, vy = 0, vz = 0;
+            if (own) {
+                slot = s_slot[is];
+                aid = (PREC == 1) ? __float_as_int(s_q[is].w) : s_id[is];
+                rx = __ldcg(B.r[p] + slot);
+                ry = __ldcg(B.r[p] + S + slot);
+                rz = __ldcg(B.r[p] + 2 * S + slot);
+                vx = __ldcg(B.v[p] + slot);
+                vy = __ldcg(B.v[p] + S + slot);
+                vz = __ldcg(B.v[p] + 2 * S + slot);
+                if (OBS) {
+                    // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
+                    const double hk = first_step ? 0.0 : 0.5 * dt;
+                    const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
+                    red_u += 0.5 * uu;
+                    red_w += 0.5 * ww;
+                    red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
+                    if (!INTEGRATE) {
+                        const long long o = 3LL * aid;
+                        B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
+                        B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
+                        B.out_r[o] = rx; B.out_r[o + 1] = ry; B.out_r[o + 2] = rz;
+                    }
+                }
+            }
+            if (INTEGRATE) {
+                long long dest = 0;
+                int cx = 0, cy = 0, cz = 0;
+                if (own) {
+                    vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
+                    vy += kick * fy;
+                    vz += kick * fz;
+                    rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
+                    ry = wrap_coord(ry + vy * dt, B.L[1]);
+                    rz = wrap_coord(rz + vz * dt, B.L[2]);
+                    cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
+                    cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
+                    cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
+                    const int dj = cx / B.cps - j;
+                    const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
+                    if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
+                    dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
+                }
+                const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
+                if (own) {
+                    if (k >= B.cap) {
+                        set_error(B.err, kErrCapacity);
+                    } else {
+                        store_atom<PREC>(B, pn, dest * B.cap + k, aid, dest, rx, ry, rz, vx, vy,
+                                         vz, cx, cy, cz);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (OBS) {
+        // fixed-order FP64 reduction: xor tree in the warp, then warps in order
+        for (int o = 16; o > 0; o >>= 1) {
+            red_u += __shfl_xor_sync(kFull, red_u, o);
+            red_w += __shfl_xor_sync(kFull, red_w, o);
+            red_k += __shfl_xor_sync(kFull, red_k, o);
+        }
+        if (lane == 0) {
+            s_red[warp * 3 + 0] = red_u;
+            s_red[warp * 3 + 1] = red_w;
+            s_red[warp * 3 + 2] = red_k;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double u = 0, w = 0, k = 0;
+            for (int q = 0; q < kWarps; ++q) {
+                u += s_red[q * 3];
+                w += s_red[q * 3 + 1];
+                k += s_red[q * 3 + 2];
+            }
+            B.unit_obs[3LL * unit_id] = u;
+            B.unit_obs[3LL * unit_id + 1] = w;
+            B.unit_obs[3LL * unit_id + 2] = k;
+        }
+    }
+}
+
+// ---- kernels ---------------------------------------------------------------
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double *pos,
+                                                  const double *vel)
+{
+    const BoxDev &B = *bp;
+    const int lane = threadIdx.x & 31;
+    const int p = (int)(B.step & 1);
+    const unsigned tag = (unsigned)(B.step + 1);
+    const long long n = B.n_atoms;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const long long i = i0 + threadIdx.x;
+        const bool own = i < n;
+        double x = 0, y = 0, z = 0, vx = 0, vy = 0, vz = 0;
+        int cx = 0, cy = 0, cz = 0;
+        long long dest = 0;
+        if (own) {
+            x = pos[3 * i]; y = pos[3 * i + 1]; z = pos[3 * i + 2];
+            x -= B.L[0] * floor(x / B.L[0]);
+            y -= B.L[1] * floor(y / B.L[1]);
+            z -= B.L[2] * floor(z / B.L[2]);
+            x = wrap_coord(x, B.L[0]);
+            y = wrap_coord(y, B.L[1]);
+            z = wrap_coord(z, B.L[2]);
+            if (vel) {
+                vx = vel[3 * i]; vy = vel[3 * i + 1]; vz = vel[3 * i + 2];
+            }
+            cx = cell_of(x, B.inv_lc[0], B.nc[0]);
+            cy = cell_of(y, B.inv_lc[1], B.nc[1]);
+            cz = cell_of(z, B.inv_lc[2], B.nc[2]);
+            dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
+        }
+        const int k = reserve_slot(B.cnt[p], dest, own, tag, lane, B.err);
+        if (own) {
+            if (k >= B.cap) set_error(B.err, kErrCapacity);
+            else store_atom<PREC>(B, p, dest * B.cap + k, (int)i, dest, x, y, z, vx, vy, vz, cx, cy, cz);
+        }
+    }
+}
+
+template <int PREC, bool INTEGRATE, bool OBS>
+__global__ void __launch_bounds__(kThreads) k_units(const BoxDev *bp, long long s_abs, int first)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ BoxDev sB;
+    if (threadIdx.x == 0) sB = *bp;
+    __syncthreads();
+    const int u = blockIdx.x;
+    const int j = u / sB.units_per_slice, tile = u - j * sB.units_per_slice;
+    run_unit<PREC, INTEGRATE, OBS>(sB, j, tile, s_abs, first != 0, u, smem);
+}
+
+__global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int n, double *out3)
+{
+    __shared__ double s[3][256];
+    double a = 0, b = 0, c = 0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        a += unit_obs[3LL * i];
+        b += unit_obs[3LL * i + 1];
+        c += unit_obs[3LL * i + 2];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    s[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + o];
+            s[1][threadIdx.x] += s[1][threadIdx.x + o];
+            s[2][threadIdx.x] += s[2][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out3[0] = s[0][0];
+        out3[1] = s[1][0];
+        out3[2] = s[2][0];
+    }
+}
+
+// The persistent ring: every CTA is one on-chip stage that repeatedly takes
+// the next ticket, waits (bounded) until the five slices its unit reads at
+// the previous level are complete, runs the unit and reports completion.
+// Tickets are dispensed step-major and, within a step, slice by slice from
+// an offset that advances two slices per step, so level s trails level s-1
+// by about five slices (the time-skewed cyclic order of Sec. 3.1 / Table 1).
+// A CTA only waits on tickets smaller than its own, all of which were taken
+// by running CTAs, so the ring always progresses.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_ring(RingPlan plan)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ BoxDev sB;
+    __shared__ long long s_ticket;
+    __shared__ int s_box;
+    __shared__ int s_go;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_box = -1;
+    __syncthreads();
+    while (true) {
+        if (tid == 0) s_ticket = (long long)atomicAdd(plan.ticket, 1ULL);
+        __syncthreads();
+        const long long t = s_ticket;
+        if (t >= plan.total) break;
+        // decode: relative step, box, unit within the box's step
+        int lo = 0, hi = plan.n_steps - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (plan.step_base[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const int s_rel = lo;
+        const long long r = t - plan.step_base[s_rel];
+        int bl = 0, bh = plan.active[s_rel] - 1;
+        while (bl < bh) {
+            const int mid = (bl + bh + 1) >> 1;
+            if (plan.cum_units[mid] <= r) bl = mid; else bh = mid - 1;
+        }
+        const int b = bl;
+        const long long m = r - plan.cum_units[b];
+        if (b != s_box) {
+            __syncthreads();
+            if (tid == 0) {
+                sB = plan.boxes[b];
+                s_box = b;
+            }
+            __syncthreads();
+        }
+        const long long s_abs = sB.step + s_rel;
+        const int ups = sB.units_per_slice;
+        const int jj = (int)(m / ups), tile = (int)(m - (long long)jj * ups);
+        const int j = ring_slice(jj, s_abs, sB.n_slices);
+        // bounded wait for slices j-2..j+2 at the previous level.  A box that
+        // has already failed (capacity, migration) drains its remaining units
+        // without work so that nothing waits on it; a wait that expires stops
+        // the whole launch and marks every box of it.
+        if (tid == 0) {
+            int go = 1;   // 0: stop the CTA, 1: run the unit, 2: skip it
+            if (ld_volatile_int(plan.err) != 0) go = 0;
+            else if (ld_volatile_int(sB.err) != 0) go = 2;
+            if (go == 1 && s_rel > 0) {
+                const unsigned need = (unsigned)ups * (unsigned)s_rel;
+                const unsigned long long t0 = global_ns();
+                for (int d = -2; d <= 2 && go == 1; ++d) {
+                    const int k = wrap_index(j + d, sB.n_slices);
+                    unsigned sleep = 32;
+                    while (ld_acquire(sB.done + k) < need) {
+                        if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
+                        if ((long long)(global_ns() - t0) > sB.wait_limit_ns) {
+                            atomicCAS(plan.err, 0, kErrTimeout);
+                            for (int q = 0; q < plan.n_boxes; ++q) set_error(plan.boxes[q].err, kErrTimeout);
+                            go = 0;
+                            break;
+                        }
+                        __nanosleep(sleep);
+                        if (sleep < 1024) sleep <<= 1;
+                    }
+                }
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (s_go == 0) break;
+        if (s_go == 1)
+            run_unit<PREC, true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && !(j == sB.withhold_slice && s_rel == 0)) atomicAdd(sB.done + j, 1u);
+    }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t unit_smem_bytes(int precision, int staged_cells, int smem_atoms)
+{
+    return make_layout(precision, staged_cells, smem_atoms).total;
+}
+
+size_t max_unit_smem_bytes()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // the kernels also hold a static copy of the box descriptor and a few words
+    return (size_t)v > 4096 ? (size_t)v - 4096 : 0;
+}
+
+cudaError_t launch_bin(const BoxDev &hb, const BoxDev *db, const double *pos, const double *vel,
+                       cudaStream_t stream)
+{
+    if (hb.n_atoms == 0) return cudaSuccess;
+    const long long blocks = (hb.n_atoms + kThreads - 1) / kThreads;
+    const int grid = (int)(blocks < 65535 ? blocks : 65535);
+    if (hb.precision == 1) k_bin<1><<<grid, kThreads, 0, stream>>>(db, pos, vel);
+    else k_bin<0><<<grid, kThreads, 0, stream>>>(db, pos, vel);
+    return cudaGetLastError();
+}
+
+template <int PREC, bool INTEGRATE, bool OBS>
+static cudaError_t launch_units(const BoxDev &hb, const BoxDev *db, long long s_abs, int first,
+                                cudaStream_t stream)
+{
+    const size_t smem = unit_smem_bytes(PREC, hb.staged_cells, hb.smem_atoms);
+    cudaError_t e = set_smem(k_units<PREC, INTEGRATE, OBS>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = hb.n_slices * hb.units_per_slice;
+    k_units<PREC, INTEGRATE, OBS><<<grid, kThreads, smem, stream>>>(db, s_abs, first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const BoxDev &hb, const BoxDev *db, int64_t s_abs, int first_step,
+                        cudaStream_t stream)
+{
+    return hb.precision == 1 ? launch_units<1, true, false>(hb, db, s_abs, first_step, stream)
+                             : launch_units<0, true, false>(hb, db, s_abs, first_step, stream);
+}
+
+cudaError_t launch_force_pass(const BoxDev &hb, const BoxDev *db, cudaStream_t stream)
+{
+    return hb.precision == 1 ? launch_units<1, false, true>(hb, db, hb.step, hb.w_is_sync, stream)
+                             : launch_units<0, false, true>(hb, db, hb.step, hb.w_is_sync, stream);
+}
+
+cudaError_t launch_obs_reduce(const double *unit_obs, int n_units, double *out3, cudaStream_t stream)
+{
+    k_obs_reduce<<<1, 256, 0, stream>>>(unit_obs, n_units, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ring(const RingPlan &plan, int precision, size_t smem_bytes, int ctas,
+                        cudaStream_t stream)
+{
+    if (plan.total == 0) return cudaSuccess;
+    cudaError_t e;
+    if (precision == 1) {
+        e = set_smem(k_ring<1>, smem_bytes);
+        if (e != cudaSuccess) return e;
+        k_ring<1><<<ctas, kThreads, smem_bytes, stream>>>(plan);
+    } else {
+        e = set_smem(k_ring<0>, smem_bytes);
+        if (e != cudaSuccess) return e;
+        k_ring<0><<<ctas, kThreads, smem_bytes, stream>>>(plan);
+    }
+    return cudaGetLastError();
+}
+
+int ring_ctas_per_sm(int precision, size_t smem_bytes)
+{
+    int n = 0;
+    if (precision == 1) {
+        set_smem(k_ring<1>, smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring<1>, kThreads, smem_bytes);
+    } else {
+        set_smem(k_ring<0>, smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring<0>, kThreads, smem_bytes);
+    }
+    return n;
+}
+
+}  // namespace dsea

@@ -1,0 +1,327 @@
+// dsea_server.cu -- continuous-batching server for many LJ boxes.
+//
+// Jobs (a box description and a step count) queue in arrival order.  A host
+// thread admits them while their estimated device footprint fits the memory
+// budget, creates and bins their boxes (state stays resident on the device),
+// and advances every resident box together in one persistent ring launch of
+// at most `segment_steps` steps per box.  Between launches, finished jobs are
+// read back and released and newly arrived jobs join, so jobs that arrive
+// while others run overlap with them on the device.  Each box is advanced by
+// exactly the arithmetic it would see alone: the kernels sum every force in
+// an order fixed by the box's own state, so a job's result does not depend on
+// which other jobs shared its launches.
+#include "dsea_host.h"
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct Job {
+    uint64_t id = 0;
+    dsea_box_desc desc{};
+    std::vector<double> pos, vel;
+    int64_t steps = 0, remaining = 0;
+    size_t bytes = 0;
+    double t_arrive = 0, t_start = -1, t_done = -1;
+    int state = 0;   // 0 queued, 1 running, 2 done, < 0 error
+    dsea_box *box = nullptr;
+    std::vector<double> pos_out, vel_out;
+    dsea_observables obs{};
+};
+
+}  // namespace
+
+struct dsea_server {
+    size_t budget = 0;
+    dsea_params params{};
+    int segment = 100;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Job *> queue;
+    std::map<uint64_t, Job *> jobs;
+    size_t used = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    int unfinished = 0;
+    double atom_steps = 0, busy_s = 0;
+    int launches = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::thread worker;
+    dsea::MultiPlan mp;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void finish(dsea_server *s, Job *j, int state)
+{
+    if (j->box) {
+        dsea_box_destroy(j->box);
+        j->box = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->used -= j->bytes;
+    j->state = state;
+    j->t_done = s->now();
+    --s->unfinished;
+    s->cv_done.notify_all();
+}
+
+int start_job(dsea_server *s, Job *j)
+{
+    dsea_box_desc d = j->desc;
+    d.pos = j->pos.data();
+    d.vel = j->vel.empty() ? nullptr : j->vel.data();
+    int rc = dsea_box_create(&d, nullptr, s->stream, &j->box);
+    if (!rc) rc = dsea_register_kernel(j->box, DSEA_KERNEL_LJ_TS, 1, 1, &s->params);
+    if (!rc) {
+        j->pos.clear();
+        j->pos.shrink_to_fit();
+        j->vel.clear();
+        j->vel.shrink_to_fit();
+    }
+    return rc;
+}
+
+void run(dsea_server *s)
+{
+    cudaSetDevice(s->device);
+    std::vector<Job *> running;
+    while (true) {
+        std::vector<Job *> admitted;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            while (!s->stop && s->queue.empty() && running.empty()) s->cv_work.wait(lk);
+            if (s->stop) break;
+            // admit in arrival order while the head of the queue fits the budget
+            while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
+                Job *j = s->queue.front();
+                s->queue.pop_front();
+                s->used += j->bytes;
+                j->state = 1;
+                j->t_start = s->now();
+                admitted.push_back(j);
+            }
+        }
+        for (Job *j : admitted) {
+            const int rc = start_job(s, j);
+            if (rc) finish(s, j, rc);
+            else if (j->remaining == 0) {
+                j->pos_out.resize(3 * j->desc.n_atoms);
+                j->vel_out.resize(3 * j->desc.n_atoms);
+                const int r2 = dsea::read_state(j->box, j->pos_out.data(), j->vel_out.data(), &j->obs);
+                finish(s, j, r2 ? r2 : 2);
+            } else {
+                running.push_back(j);
+            }
+        }
+        if (running.empty()) continue;
+        // one persistent launch over every resident box
+        const int n = (int)running.size();
+        std::vector<dsea_box *> boxes(n);
+        std::vector<int64_t> steps(n);
+        double work = 0;
+        for (int k = 0; k < n; ++k) {
+            boxes[k] = running[k]->box;
+            steps[k] = std::min<int64_t>(running[k]->remaining, s->segment);
+            work += (double)running[k]->desc.n_atoms * (double)steps[k];
+        }
+        int rc = dsea::multi_prepare(s->mp, boxes.data(), steps.data(), n);
+        if (!rc) {
+            cudaEventRecord(s->ev0, s->stream);
+            rc = dsea::multi_enqueue(s->mp, boxes.data(), s->stream);
+            cudaEventRecord(s->ev1, s->stream);
+        }
+        if (!rc) {
+            dsea::multi_commit(boxes.data(), steps.data(), n);
+            if (cudaEventSynchronize(s->ev1) != cudaSuccess) rc = DSEA_ERR_CUDA;
+        }
+        if (!rc) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->busy_s += ms * 1e-3;
+            s->atom_steps += work;
+            s->launches += 1;
+        }
+        std::vector<Job *> still;
+        for (int k = 0; k < n; ++k) {
+            Job *j = running[k];
+            int jrc = rc ? rc : dsea_sync(j->box);
+            if (!jrc) j->remaining -= steps[k];
+            if (jrc) {
+                finish(s, j, jrc);
+            } else if (j->remaining == 0) {
+                j->pos_out.resize(3 * j->desc.n_atoms);
+                j->vel_out.resize(3 * j->desc.n_atoms);
+                const int r2 = dsea::read_state(j->box, j->pos_out.data(), j->vel_out.data(), &j->obs);
+                finish(s, j, r2 ? r2 : 2);
+            } else {
+                still.push_back(j);
+            }
+        }
+        running.swap(still);
+    }
+    for (Job *j : running) finish(s, j, DSEA_ERR_STATE);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int segment_steps,
+                       void *cuda_stream, dsea_server **out)
+{
+    if (!out || mem_budget_bytes == 0 || segment_steps <= 0) return DSEA_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DSEA_ERR_NO_DEVICE;
+    }
+    dsea_server *s = new (std::nothrow) dsea_server();
+    if (!s) return DSEA_ERR_OOM;
+    s->budget = mem_budget_bytes;
+    s->params = params ? *params : dsea_params{2.5, 0.005, DSEA_MIXED, DSEA_SCHED_RING, 0, 0, 0, 0};
+    s->segment = segment_steps;
+    s->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&s->device);
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return DSEA_ERR_CUDA;
+    }
+    s->worker = std::thread(run, s);
+    *out = s;
+    return DSEA_OK;
+}
+
+double dsea_server_clock(const dsea_server *s)
+{
+    return s ? s->now() : 0.0;
+}
+
+int dsea_server_submit(dsea_server *s, const dsea_box_desc *desc, int64_t steps, uint64_t *job_id)
+{
+    if (!s || !desc || !job_id || steps < 0 || desc->n_atoms < 0) return DSEA_ERR_INVALID_ARG;
+    if (desc->n_atoms > 0 && !desc->pos) return DSEA_ERR_INVALID_ARG;
+    size_t bytes = 0;
+    int rc = dsea::estimate_box_bytes(desc, &s->params, &bytes);
+    if (rc) return rc;
+    if (bytes > s->budget) return DSEA_ERR_BUDGET;
+    Job *j = new (std::nothrow) Job();
+    if (!j) return DSEA_ERR_OOM;
+    j->desc = *desc;
+    j->pos.assign(desc->pos, desc->pos + 3 * desc->n_atoms);
+    if (desc->vel) j->vel.assign(desc->vel, desc->vel + 3 * desc->n_atoms);
+    j->desc.pos = nullptr;
+    j->desc.vel = nullptr;
+    j->steps = j->remaining = steps;
+    j->bytes = bytes;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete j;
+            return DSEA_ERR_STATE;
+        }
+        j->id = s->next_id++;
+        j->t_arrive = s->now();
+        s->jobs[j->id] = j;
+        s->queue.push_back(j);
+        ++s->unfinished;
+        *job_id = j->id;
+    }
+    s->cv_work.notify_one();
+    return DSEA_OK;
+}
+
+int dsea_server_poll(dsea_server *s, uint64_t job_id, int *state)
+{
+    if (!s || !state) return DSEA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return DSEA_ERR_NOT_FOUND;
+    *state = it->second->state;
+    return DSEA_OK;
+}
+
+int dsea_server_result(dsea_server *s, uint64_t job_id, double *pos, double *vel,
+                       dsea_observables *obs, double *t_arrive, double *t_done)
+{
+    if (!s) return DSEA_ERR_INVALID_ARG;
+    Job *j = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(job_id);
+        if (it == s->jobs.end()) return DSEA_ERR_NOT_FOUND;
+        j = it->second;
+        if (j->state == 0 || j->state == 1) return DSEA_ERR_STATE;
+        s->jobs.erase(it);
+    }
+    const int state = j->state;
+    if (state == 2) {
+        const size_t nb = sizeof(double) * 3 * (size_t)j->desc.n_atoms;
+        if (pos && nb) std::copy(j->pos_out.begin(), j->pos_out.end(), pos);
+        if (vel && nb) std::copy(j->vel_out.begin(), j->vel_out.end(), vel);
+        if (obs) *obs = j->obs;
+    }
+    if (t_arrive) *t_arrive = j->t_arrive;
+    if (t_done) *t_done = j->t_done;
+    delete j;
+    return state == 2 ? DSEA_OK : state;
+}
+
+int dsea_server_drain(dsea_server *s)
+{
+    if (!s) return DSEA_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->unfinished == 0 || s->stop; });
+    return DSEA_OK;
+}
+
+int dsea_server_stats(const dsea_server *s, double *atom_steps, double *busy_seconds, int *launches)
+{
+    if (!s) return DSEA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(const_cast<dsea_server *>(s)->mu);
+    if (atom_steps) *atom_steps = s->atom_steps;
+    if (busy_seconds) *busy_seconds = s->busy_s;
+    if (launches) *launches = s->launches;
+    return DSEA_OK;
+}
+
+int dsea_server_destroy(dsea_server *s)
+{
+    if (!s) return DSEA_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto &kv : s->jobs) {
+        if (kv.second->box) dsea_box_destroy(kv.second->box);
+        delete kv.second;
+    }
+    dsea::multi_free(s->mp);
+    cudaEventDestroy(s->ev0);
+    cudaEventDestroy(s->ev1);
+    delete s;
+    return DSEA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+"""Many boxes in one persistent launch, the autotuner, and the continuous-
+batching server: every box's result is the same alone and in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_11289_gb300 import dsea, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _boxes(n, seed=2):
+    specs = inputs.batch_specs(n_boxes=n, seed=seed, n_max=6000)
+    return [s.state() for s in specs]
+
+
+def _alone(state, steps, precision=dsea.MIXED):
+    pos, vel, box = state
+    with dsea.Box(pos, vel, box, precision=precision) as b:
+        b.advance(steps)
+        return b.positions(), b.velocities(), b.observables()
+
+
+def test_batch_equals_alone_bitwise():
+    states = _boxes(6)
+    steps = [40, 25, 40, 0, 13, 31]
+    ref = [_alone(s, k) for s, k in zip(states, steps)]
+    boxes = [dsea.Box(*s, precision=dsea.MIXED) for s in states]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        # two advances: the second replays the captured graph of the first shape
+        dsea.batch_advance(bt, [k // 2 for k in steps])
+        dsea.batch_advance(bt, [k - k // 2 for k in steps])
+        dsea.batch_destroy(bt)
+        for b, (r, v, o), k in zip(boxes, ref, steps):
+            assert np.array_equal(b.positions(), r)
+            assert np.array_equal(b.velocities(), v)
+            assert b.observables() == o and o["step"] == k
+    finally:
+        for b in boxes:
+            b.close()
+
+
+def test_batch_fp64_matches_oracle():
+    states = _boxes(3, seed=9)
+    boxes = [dsea.Box(*s, precision=dsea.FP64) for s in states]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        dsea.batch_advance(bt, [20, 20, 20])
+        dsea.batch_destroy(bt)
+        for b, (pos, vel, box) in zip(boxes, states):
+            ro, _, _, _ = oracle.run(pos, vel, box, steps=20)
+            d = b.positions() - ro
+            d -= box * np.round(d / box)
+            assert np.abs(d).max() <= 1e-9
+    finally:
+        for b in boxes:
+            b.close()
+
+
+def test_autotune_keeps_results_and_state():
+    pos, vel, box = inputs.SMALL_4K.state()
+    r_ref, _, _ = _alone((pos, vel, box), 30)
+    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+        b.advance(10)
+        chosen = b.autotune(trial_steps=3)
+        assert chosen["tile_y"] >= 1 and chosen["tile_z"] >= 1
+        assert b.observables()["step"] == 10          # trials left the state untouched
+        b.advance(20)
+        assert np.array_equal(b.positions(), r_ref)
+
+
+def test_server_results_same_alone_and_in_mix():
+    states = _boxes(5, seed=4)
+    steps = [60, 150, 35, 90, 120]
+    srv = dsea.server_create(8 << 30, dsea.make_params(precision=dsea.MIXED), 25, 0)
+    try:
+        # job 0 alone
+        j0 = dsea.server_submit(srv, *states[0], steps[0])
+        dsea.server_drain(srv)
+        alone = dsea.server_result(srv, j0, len(states[0][0]))
+        # job 0 again, arriving while the others run
+        ids = [dsea.server_submit(srv, *states[k], steps[k]) for k in (1, 2)]
+        time.sleep(0.01)
+        ids.insert(0, dsea.server_submit(srv, *states[0], steps[0]))
+        ids += [dsea.server_submit(srv, *states[k], steps[k]) for k in (3, 4)]
+        dsea.server_drain(srv)
+        res = {}
+        for jid, k in zip(ids, [0, 1, 2, 3, 4]):
+            assert dsea.server_poll(srv, jid) == 2
+            res[k] = dsea.server_result(srv, jid, len(states[k][0]))
+        assert np.array_equal(res[0][0], alone[0]) and np.array_equal(res[0][1], alone[1])
+        assert res[0][2] == alone[2]
+        for k in range(1, 5):
+            r, v, o = _alone(states[k], steps[k])
+            assert np.array_equal(res[k][0], r) and o == res[k][2]
+            assert res[k][4] >= res[k][3]           # done after arrival
+        st = dsea.server_stats(srv)
+        assert st["launches"] >= 2 and st["atom_steps"] > 0
+    finally:
+        dsea.server_destroy(srv)
+
+
+def test_server_rejects_job_over_budget():
+    pos, vel, box = inputs.SMALL_4K.state()
+    srv = dsea.server_create(1 << 20, None, 10, 0)          # 1 MiB budget
+    try:
+        with pytest.raises(dsea.DseaError) as e:
+            dsea.server_submit(srv, pos, vel, box, 10)
+        assert e.value.code == dsea.ERR_BUDGET
+    finally:
+        dsea.server_destroy(srv)
+
+
+def test_torch_allocator_owns_box_memory():
+    import torch
+    pos, vel, box = inputs.SMALL_4K.state()
+    before = torch.cuda.memory_allocated()
+    b = dsea.Box(pos, vel, box, precision=dsea.MIXED)
+    during = torch.cuda.memory_allocated()
+    assert during - before >= b.info()["device_bytes"] * 0.9
+    b.close()
+    assert torch.cuda.memory_allocated() == before

@@ -1,0 +1,218 @@
+"""GPU parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (written from the stated targets):
+  FP64 forces       rms_i |F_gpu - F_oracle| <= 1e-12 rms_i |F_oracle|
+  FP64 trajectory   max |r_gpu - r_oracle| <= 1e-9 sigma after 100 steps
+  mixed forces      rms_i |F_gpu - F_oracle| <= 2e-6 rms_i |F_oracle|
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_11289_gb300 import dsea, inputs
+
+pytestmark = pytest.mark.gpu
+
+RC = 2.5
+
+
+def min_image(d, box):
+    return d - box * np.round(d / box)
+
+
+def rms(a):
+    return float(np.sqrt((np.asarray(a) ** 2).sum(-1).mean()))
+
+
+def force_err(Fg, Fo):
+    return rms(Fg - Fo) / rms(Fo), float(np.sqrt(((Fg - Fo) ** 2).sum(-1)).max() / rms(Fo))
+
+
+def jittered_4k(amp=0.12, seed=7):
+    pos, vel, box = inputs.SMALL_4K.state()
+    return inputs.jitter(pos, box, amp, seed), vel, box
+
+
+@pytest.mark.parametrize("schedule", [dsea.SCHED_RING, dsea.SCHED_STEPWISE])
+@pytest.mark.parametrize("tiles", [(4, 4), (2, 3), (6, 6)])
+def test_fp64_forces_match_oracle(schedule, tiles):
+    pos, vel, box = jittered_4k()
+    Fo, Uo, Wo = oracle.forces(pos, box, RC, "cells")
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.FP64, schedule=schedule,
+                  tile_y=tiles[0], tile_z=tiles[1]) as b:
+        Fg = b.forces()
+        ob = b.observables()
+        rg = b.positions()
+    e_rms, e_max = force_err(Fg, Fo)
+    assert e_rms <= 1e-12, (e_rms, e_max)
+    assert ob["U"] == pytest.approx(Uo, rel=1e-12)
+    assert ob["W"] == pytest.approx(Wo, rel=1e-12)
+    assert ob["KE"] == pytest.approx(0.5 * (vel ** 2).sum(), rel=1e-12)
+    assert np.abs(min_image(rg - pos, box)).max() < 1e-12
+
+
+def test_mixed_forces_match_oracle(melted_4k):
+    pos, vel, box = melted_4k
+    Fo, Uo, Wo = oracle.forces(pos, box, RC, "cells")
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.MIXED) as b:
+        Fg = b.forces()
+        ob = b.observables()
+    e_rms, e_max = force_err(Fg, Fo)
+    print(f"mixed force error: rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= 2e-6
+    # U and W are sums of FP32 pair terms that cancel (W of a liquid is a small
+    # difference of terms ~ F * sigma): hold them to 2e-6 of N * F_rms * sigma
+    scale = 2e-6 * len(pos) * rms(Fo)
+    assert abs(ob["U"] - Uo) <= scale
+    assert abs(ob["W"] - Wo) <= scale
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_first_config_trajectory_100_steps(precision):
+    """4,000-atom fcc start, T* 1.5, 4 slices, 100 velocity-Verlet steps."""
+    spec = inputs.SMALL_4K
+    pos, vel, box = spec.state()
+    ro, vo, Fo, obs = oracle.run(pos, vel, box, steps=spec.steps)
+    with dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision) as b:
+        b.advance(spec.steps)
+        rg, vg, Fg, og = b.positions(), b.velocities(), b.forces(), b.observables()
+    dr = np.abs(min_image(rg - ro, box)).max()
+    dv = np.abs(vg - vo).max()
+    print(f"precision {precision}: max |dr| {dr:.3e}, max |dv| {dv:.3e}")
+    assert og["step"] == spec.steps
+    if precision == dsea.FP64:
+        assert dr <= 1e-9 and dv <= 1e-8
+        assert force_err(Fg, Fo)[0] <= 1e-10
+        assert og["U"] == pytest.approx(obs[-1, 0], rel=1e-10)
+        assert og["W"] == pytest.approx(obs[-1, 1], rel=1e-10)
+        assert og["KE"] == pytest.approx(obs[-1, 2], rel=1e-10)
+    else:
+        # mixed: trajectories separate chaotically; they stay close over 100 steps
+        assert dr <= 1e-4
+        assert og["U"] + og["KE"] == pytest.approx(obs[-1, 0] + obs[-1, 2], abs=1e-3 * len(pos))
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_ring_equals_stepwise_bitwise(precision, melted_4k):
+    pos, vel, box = melted_4k
+    out = []
+    for sched in (dsea.SCHED_RING, dsea.SCHED_STEPWISE):
+        with dsea.Box(pos, vel, box, n_slices=4, precision=precision, schedule=sched) as b:
+            b.advance(25)
+            b.advance(15)
+            out.append((b.positions(), b.velocities(), b.observables()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+def test_unit_shape_does_not_change_results(melted_4k):
+    pos, vel, box = melted_4k
+    ref = None
+    for ty, tz in [(1, 1), (2, 5), (4, 4), (6, 6)]:
+        with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.MIXED, tile_y=ty, tile_z=tz) as b:
+            b.advance(20)
+            r = b.positions()
+        if ref is None:
+            ref = r
+        assert np.array_equal(r, ref), (ty, tz)
+
+
+@pytest.mark.parametrize("n_slices", [3, 4, 6])
+def test_slice_count_fp64_parity(n_slices, melted_4k):
+    pos, vel, box = melted_4k
+    ro, vo, _, _ = oracle.run(pos, vel, box, steps=30)
+    with dsea.Box(pos, vel, box, n_slices=n_slices, precision=dsea.FP64) as b:
+        assert b.info()["n_slices"] == n_slices
+        b.advance(30)
+        rg = b.positions()
+    assert np.abs(min_image(rg - ro, box)).max() <= 1e-9
+
+
+def test_mixed_energy_drift_1000_steps(melted_4k):
+    """NVE drift of the mixed form over 1000 steps, next to the oracle's own."""
+    pos, vel, box = melted_4k
+    n = len(pos)
+    e_gpu = []
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.MIXED) as b:
+        for _ in range(100):
+            o = b.observables()
+            e_gpu.append((o["U"] + o["KE"]) / n)
+            b.advance(10)
+        o = b.observables()
+        e_gpu.append((o["U"] + o["KE"]) / n)
+    _, _, _, obs = oracle.run(pos, vel, box, steps=1000)
+    e_ora = (obs[::10, 0] + obs[::10, 2]) / n
+    e_gpu = np.array(e_gpu)
+    drift_gpu = abs(e_gpu[-10:].mean() - e_gpu[:10].mean())
+    drift_ora = abs(e_ora[-10:].mean() - e_ora[:10].mean())
+    print(f"drift per atom over 1000 steps: mixed {drift_gpu:.3e}, oracle FP64 {drift_ora:.3e}; "
+          f"max |E-E0| mixed {np.abs(e_gpu - e_gpu[0]).max():.3e}")
+    assert drift_gpu <= max(1e-4, 2.0 * drift_ora)
+
+
+def test_smallest_box_and_ragged_units():
+    # 3 cells per axis (the minimum) and a 7-cell axis cut by 4-cell units
+    pos, box = inputs.fcc_lattice(5, 0.8)            # 8.55 edge: 3 cells
+    pos = inputs.jitter(pos, box, 0.1, 3)
+    vel = inputs.maxwell_boltzmann(len(pos), 1.2, 4)
+    ro, vo, _, _ = oracle.run(pos, vel, box, steps=20)
+    with dsea.Box(pos, vel, box, precision=dsea.FP64) as b:
+        assert b.info()["cells"] == [3, 3, 3]
+        b.advance(20)
+        assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
+    pos, box = inputs.fcc_lattice(10, 0.55)          # 19.4 edge: 7 cells
+    pos = inputs.jitter(pos, box, 0.1, 5)
+    vel = inputs.maxwell_boltzmann(len(pos), 1.0, 6)
+    ro, _, _, _ = oracle.run(pos, vel, box, steps=20)
+    with dsea.Box(pos, vel, box, precision=dsea.FP64, tile_y=4, tile_z=3) as b:
+        assert b.info()["cells"] == [7, 7, 7]
+        b.advance(20)
+        assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
+
+
+def test_empty_single_atom_and_free_flight():
+    box = np.array([9.0, 9.0, 9.0])
+    with dsea.Box(np.zeros((0, 3)), None, box) as b:
+        b.advance(5)
+        assert b.positions().shape == (0, 3)
+        assert b.observables() == {"step": 5, "U": 0.0, "W": 0.0, "KE": 0.0}
+    pos = np.array([[1.0, 2.0, 3.0], [6.0, 6.0, 6.0]])
+    vel = np.array([[0.5, -0.25, 1.0], [0.0, 0.0, 0.0]])
+    with dsea.Box(pos, vel, box) as b:
+        b.advance(40)
+        r = b.positions()
+        assert np.allclose(r[0], np.mod(pos[0] + 40 * 0.005 * vel[0], box), atol=1e-13)
+        assert np.array_equal(b.velocities(), vel) and np.all(b.forces() == 0)
+
+
+def test_dimer_across_periodic_boundary():
+    box = np.array([9.0, 9.0, 9.0])
+    pos = np.array([[0.3, 1.0, 8.8], [8.6, 1.0, 0.1]])
+    Fo, Uo, Wo = oracle.forces(pos, box, RC, "brute")
+    for prec in (dsea.FP64, dsea.MIXED):
+        with dsea.Box(pos, None, box, precision=prec) as b:
+            Fg = b.forces()
+            tol = 1e-12 if prec == dsea.FP64 else 2e-6
+            assert np.abs(Fg - Fo).max() <= tol * np.abs(Fo).max()
+            assert b.observables()["U"] == pytest.approx(Uo, rel=10 * tol)
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_full_1m_box_sampled_atoms(precision):
+    """1,048,576-atom box (64^3 fcc cells, rho 0.8), 43 slices, in the launch
+    form the benchmark times; forces at 256 sampled atoms against the oracle,
+    plus Newton's third law over all atoms."""
+    spec = inputs.FLUID_1M
+    pos, vel, box = spec.state()
+    pos = inputs.jitter(pos, box, 0.1, 17)
+    rng = np.random.Generator(np.random.PCG64(5))
+    idx = np.sort(rng.choice(len(pos), 256, replace=False))
+    Fo, _, _ = oracle.forces_subset(pos, box, idx, RC)
+    with dsea.Box(pos, vel, box, precision=precision) as b:
+        info = b.info()
+        assert info["n_slices"] == 43 and info["cells"] == [43, 43, 43]
+        Fg = b.forces()
+    tol = 1e-12 if precision == dsea.FP64 else 2e-6
+    assert rms(Fg[idx] - Fo) <= tol * rms(Fo)
+    assert np.abs(Fg.sum(0)).max() <= (1e-9 if precision == dsea.FP64 else 1e-3) * rms(Fg) * np.sqrt(len(pos))
