@@ -213,6 +213,36 @@ int dsea_server_stats(const dsea_server *srv, double *atom_steps, double *busy_s
 
 int dsea_server_destroy(dsea_server *srv);
 
+/* ---- forces without device allocation ------------------------------------ */
+
+/* The paper has no counterpart to this call.  It is for callers that cannot
+ * let a library allocate device memory: hosts that reserve all GPU memory in
+ * their own pool up front and refuse outside cudaMalloc calls, and
+ * latency-bound loops where cudaMalloc / cudaFree would synchronise the device.
+ * It computes, for one configuration, the forces and (U, W, KE) that a box
+ * registered with DSEA_KERNEL_LJ_TS would report at its current step, using
+ * the same kernels, but it allocates nothing: its scratch is one fixed 64 MiB
+ * device array that the library holds on every GPU that loads it until the
+ * process exits.
+ *   pos_dev   device, 3 n_atoms FP64 positions (AoS, atom-ID order), read only;
+ *   vel_dev   device, 3 n_atoms FP64 velocities, or NULL (then KE = 0);
+ *   box       host, 3 edge lengths; one slice per cell layer, cells >= rc;
+ *   precision DSEA_FP64 or DSEA_MIXED;
+ *   forces_dev device, 3 n_atoms FP64 output (atom-ID order);
+ *   obs3_dev  device, 3 FP64 outputs (U, W, KE), or NULL;
+ *   cuda_stream work is queued there; the call returns when it has finished.
+ * Returns DSEA_ERR_SCRATCH_LIMIT, before touching the GPU, when the box needs
+ * more than the 64 MiB (at density 0.8: about 290,000 atoms in FP64, 240,000
+ * in the mixed form).  The
+ * first call on a device looks up the array's device address (make it before
+ * any stream capture).  Every call shares the array: calls that overlap on the
+ * GPU, from other streams or host threads, race and must be serialised by
+ * the caller. */
+#define DSEA_ERR_SCRATCH_LIMIT -11 /* problem larger than the fixed scratch */
+int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev, int64_t n_atoms,
+                        const double *box, double rc, int precision, double *forces_dev,
+                        double *obs3_dev, void *cuda_stream);
+
 /* ---- failure-detection testing hooks -------------------------------------- */
 
 /* No GPU fault is involved.  DSEA_DEBUG_WITHHOLD_SLICE: during the next ring

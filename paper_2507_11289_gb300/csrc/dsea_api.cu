@@ -335,6 +335,7 @@ const char *dsea_status_string(int s)
     case DSEA_ERR_STATE: return "call out of order";
     case DSEA_ERR_NOT_FOUND: return "unknown job";
     case DSEA_ERR_NO_DEVICE: return "no CUDA device";
+    case DSEA_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed no-allocation scratch";
     default: return "unknown status";
     }
 }
@@ -927,6 +928,16 @@ int read_state(dsea_box *b, double *pos, double *vel, dsea_observables *obs)
         obs->KE = b->obs3[2];
     }
     return DSEA_OK;
+}
+
+}  // namespace dsea
+
+namespace dsea {
+
+int box_geometry(int n_slices, const double *L, int64_t n_atoms, dsea_params &p, BoxDev &hb)
+{
+    double mean_cap = 0;
+    return setup_geometry(n_slices, L, n_atoms, p, hb, mean_cap);
 }
 
 }  // namespace dsea

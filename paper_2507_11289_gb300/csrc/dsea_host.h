@@ -69,6 +69,9 @@ int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t stream);
 void multi_commit(dsea_box *const *boxes, const int64_t *steps, int n);
 void multi_free(MultiPlan &mp);
 
+// Geometry, cell capacity and work-unit shape of a box (no allocation).
+int box_geometry(int n_slices, const double *L, int64_t n_atoms, dsea_params &p, BoxDev &hb);
+
 // Device bytes a box of this description would hold once registered.
 int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, size_t *bytes);
 

@@ -27,6 +27,7 @@ ERR_BUDGET = -7
 ERR_STATE = -8
 ERR_NOT_FOUND = -9
 ERR_NO_DEVICE = -10
+ERR_SCRATCH_LIMIT = -11
 
 FP64 = 0
 MIXED = 1
@@ -104,6 +105,7 @@ _SIGS = {
     "dsea_server_stats": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "dsea_server_destroy": (_I, [_P]),
     "dsea_debug_set": (_I, [_P, _I, _I64]),
+    "dsea_forces_noalloc": (_I, [_P, _P, _I64, _P, _D, _I, _P, _P, _P]),
     "dsea_ring_order": (_I, [_I, _I, _I64, _I64, _P, _P]),
 }
 
