@@ -65,24 +65,25 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op_name):
+    """All-reduce one host number over the ranks (timings and counts only;
+    the replicas exchange no simulation data)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    return _reduce(x, world, "MAX")
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, "SUM")
 
 
 # ---- clocks during the timed region --------------------------------------------
@@ -401,6 +402,18 @@ def main():
         v64 = sum_over_ranks(spec.n_atoms * args.md_steps * args.fp64_steps, world) / sec64
         line["fp64"] = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
                         "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+    if "67m" not in skip:
+        big = inputs.FLUID_67M
+        sec_b, _, _, info_b = time_box(dsea, torch, big, dsea.MIXED, 1, 3, big.steps, flush_buf, stream)
+        sec_b = max_over_ranks(sec_b, world)
+        v_b = sum_over_ranks(big.n_atoms * big.steps, world) / sec_b
+        ach_b = big.n_atoms * big.steps * PAIRS_PER_ATOM(big.rho) * FLOPS_PER_PAIR / sec_b / 1e12
+        line["box_67m"] = {"value": v_b, "unit": UNIT, "md_steps": big.steps, "seconds": sec_b,
+                           "roofline_frac": ach_b / FP32_PEAK_TFLOPS, "achieved_tflops": ach_b,
+                           "workload": "LJ fluid 67,108,864 atoms (256^3 fcc), rho 0.8, T 1.5, 175 "
+                                       "x-slices, mixed, ring schedule, one 200-step advance",
+                           "unit_shape": [info_b["tile_y"], info_b["tile_z"]],
+                           "device_bytes": info_b["device_bytes"]}
     if "batch" not in skip:
         line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream)
     if "serve" not in skip:

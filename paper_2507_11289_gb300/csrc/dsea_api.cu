@@ -408,11 +408,17 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
         hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * hb.n_cells);
         hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
         hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
-        hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        hb.v[q] = nullptr;
+        hb.vf[q] = nullptr;
         hb.q[q] = nullptr;
-        if (p.precision == DSEA_MIXED) hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
-        if (!hb.cnt[q] || !hb.id[q] || !hb.r[q] || !hb.v[q] ||
-            (p.precision == DSEA_MIXED && !hb.q[q]))
+        if (p.precision == DSEA_MIXED) {
+            hb.vf[q] = (float *)dev_alloc(b, sizeof(float) * 3 * hb.n_slots);
+            hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
+        } else {
+            hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        }
+        if (!hb.cnt[q] || !hb.id[q] || !hb.r[q] ||
+            (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : !hb.v[q]))
             return DSEA_ERR_OOM;
         CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * hb.n_cells, b->stream));
     }
@@ -675,9 +681,11 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         const int sync0 = hb.w_is_sync;
         const size_t b_cnt = sizeof(unsigned long long) * hb.n_cells, b_id = sizeof(int) * hb.n_slots,
                      b_r = sizeof(double) * 3 * hb.n_slots, b_q = sizeof(float4) * hb.n_slots;
+        const bool mixed = hb.precision == DSEA_MIXED;
+        const size_t b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
         void *s_cnt = nullptr, *s_id = nullptr, *s_r = nullptr, *s_v = nullptr, *s_q = nullptr;
         bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess && cudaMalloc(&s_id, b_id) == cudaSuccess &&
-                  cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_r) == cudaSuccess &&
+                  cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_v) == cudaSuccess &&
                   (hb.precision != DSEA_MIXED || cudaMalloc(&s_q, b_q) == cudaSuccess);
         auto release = [&]() {
             cudaFree(s_cnt); cudaFree(s_id); cudaFree(s_r); cudaFree(s_v);
@@ -696,7 +704,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
             cudaError_t e = c(s_cnt, hb.cnt[p], b_cnt);
             if (e == cudaSuccess) e = c(s_id, hb.id[p], b_id);
             if (e == cudaSuccess) e = c(s_r, hb.r[p], b_r);
-            if (e == cudaSuccess) e = c(s_v, hb.v[p], b_r);
+            if (e == cudaSuccess) e = c(s_v, mixed ? (void *)hb.vf[p] : (void *)hb.v[p], b_v);
             if (e == cudaSuccess && s_q) e = c(s_q, hb.q[p], b_q);
             if (e == cudaSuccess && !save)   // stale counts of the other buffer must not match
                 e = cudaMemsetAsync(hb.cnt[p ^ 1], 0, b_cnt, b->stream);
@@ -903,7 +911,8 @@ int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, siz
     double mean_cap = 0;
     int rc = setup_geometry(desc->n_slices, desc->box, desc->n_atoms, p, hb, mean_cap);
     if (rc) return rc;
-    const size_t per_slot = sizeof(int) + 6 * sizeof(double) + (p.precision == DSEA_MIXED ? sizeof(float4) : 0);
+    const size_t per_slot = sizeof(int) + 3 * sizeof(double) +
+                            (p.precision == DSEA_MIXED ? 3 * sizeof(float) + sizeof(float4) : 3 * sizeof(double));
     size_t b = 2 * ((size_t)hb.n_cells * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
     b += (size_t)hb.n_cells * 3 * sizeof(double);              // unit partials
     b += (size_t)desc->n_atoms * 9 * sizeof(double);           // read-back arrays

@@ -49,7 +49,8 @@ struct BoxDev {
     unsigned long long *cnt[2];  // per cell: (tag << 32) | count, tag = step + 1
     int *id[2];
     double *r[2];   // absolute positions, 3 * n_slots
-    double *v[2];   // velocities (half-step after the first step), 3 * n_slots
+    double *v[2];   // FP64 form: velocities (half-step after the first step), 3 * n_slots
+    float *vf[2];   // mixed form: the same velocities in FP32, 3 * n_slots
     float4 *q[2];   // mixed: cell-centred FP32 coordinates, atom id bits in .w
     // per advance
     int64_t step;   // absolute step of the current state

@@ -15,18 +15,20 @@
 //      j+1 (O_out = 1, Sec. 4); warp-aggregated atomics reserve the slots,
 //   5. (OBS) reduces U, W and KE of its home atoms in FP64 ("stat_collect").
 //
-// The FP64 form evaluates pairs on absolute positions; the mixed form on
-// FP32 coordinates relative to each atom's cell centre, with FP64 kept for
-// absolute positions, the position update and every reduction.
+// The FP64 form evaluates pairs on absolute positions and keeps velocities in
+// FP64.  The mixed form evaluates pairs in packed FP32x2 arithmetic on FP32
+// coordinates relative to each atom's cell centre and keeps velocities in
+// FP32; FP64 is kept for the absolute positions, the position update and
+// every reduction (FP64 issues at a small fraction of the FP32 rate on this
+// GPU, so the mixed form spends about a dozen FP64 operations per atom-step).
 #include "dsea_internal.h"
-
-#include <cstdio>
 
 namespace dsea {
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPrefBytes = 32 * (3 * 8 + 3 * 4);   // per warp: own atoms' r (FP64) and v (FP32)
 
 __device__ __forceinline__ void set_error(int *err, int code)
 {
@@ -59,11 +61,28 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// Asynchronous global -> shared copies (L2 only, so data other CTAs wrote
+// during the same launch is seen).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Shared-memory carve-up of one unit.
 struct Layout {
-    size_t cnt, start, gcell, atoms, id, slot, scr, red, total;
+    size_t cnt, start, gcell, atoms, id, slot, scr, ctab, red, ctr, total;
 };
 
 __host__ __device__ inline Layout make_layout(int precision, int staged_cells, int smem_atoms)
@@ -85,8 +104,11 @@ __host__ __device__ inline Layout make_layout(int precision, int staged_cells, i
     }
     L.slot = o; o += sizeof(int) * smem_atoms;
     o = align16(o);
-    L.scr = o;  o += sizeof(double) * kThreads * 5;
+    L.scr = o;                                  // FP64: partial sums; mixed: r/v prefetch
+    o += precision == 1 ? (size_t)kWarps * kPrefBytes : sizeof(double) * kThreads * 5;
+    L.ctab = o; o += sizeof(double) * kWarps * 9;   // mixed: neighbour cell centres
     L.red = o;  o += sizeof(double) * kWarps * 3;
+    L.ctr = o;  o += 16;
     L.total = align16(o);
     return L;
 }
@@ -96,39 +118,146 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
-// Force accumulators of one lane.
-template <typename T>
-struct Acc {
-    T fx, fy, fz, u, w;
+// Force accumulators of one lane (FP64 form).
+struct Acc64 {
+    double fx, fy, fz, u, w;
 };
 
-// One candidate pair in FP32 (mixed form).  The lane's home atom, already
-// moved into the neighbour cell's frame, is (xs, ys, zs).
-template <bool OBS>
-__device__ __forceinline__ void pair_f32(float xs, float ys, float zs, const float4 pj, float rc2,
-                                         float ushift, Acc<float> &a)
+// Packed FP32x2 arithmetic (sm_100+): two pairs' worth of FP32 work per
+// issued instruction, each half rounded exactly as its scalar counterpart.
+#define DSEA_F2_OP(NAME, OP)                                                                \
+    __device__ __forceinline__ float2 NAME(float2 a, float2 b)                              \
+    {                                                                                       \
+        float2 d;                                                                           \
+        asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t" OP \
+            " rd, ra, rb;\n\tmov.b64 {%0,%1}, rd;}"                                         \
+            : "=f"(d.x), "=f"(d.y)                                                          \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                      \
+        return d;                                                                           \
+    }
+DSEA_F2_OP(f2add, "add.rn.f32x2")
+DSEA_F2_OP(f2sub, "sub.rn.f32x2")
+DSEA_F2_OP(f2mul, "mul.rn.f32x2")
+#undef DSEA_F2_OP
+
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c)
 {
-    const float dx = xs - pj.x, dy = ys - pj.y, dz = zs - pj.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    const bool in = (r2 <= rc2) & (r2 > 0.f);
-    const float r2i = rcp_approx(in ? r2 : 1.f);
-    const float r6i = r2i * r2i * r2i;
-    float fs = r2i * r6i * fmaf(48.f, r6i, -24.f);   // F_abs = 24 (2 r^-12 - r^-6) / r^2
-    fs = in ? fs : 0.f;
-    a.fx = fmaf(dx, fs, a.fx);
-    a.fy = fmaf(dy, fs, a.fy);
-    a.fz = fmaf(dz, fs, a.fz);
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
+        "mov.b64 rc, {%6,%7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 f2splat(float x) { return make_float2(x, x); }
+
+// Unrolling of the 27-cell stencil loops of the mixed force routine.
+#ifndef DSEA_CELL_UNROLL
+#define DSEA_CELL_UNROLL _Pragma("unroll 1")
+#endif
+
+// 0 < r2 <= rc2 on the bit patterns of non-negative floats (excludes the atom
+// itself, at r2 == 0, in the same test as the cutoff).
+__device__ __forceinline__ bool in_cutoff(float r2, unsigned rc2_bits)
+{
+    return (__float_as_uint(r2) - 1u) < rc2_bits;
+}
+
+// Mixed-form forces on the atoms of one home cell chunk (nin <= 32 atoms
+// starting at staged index `base`), warp-wide.  Each lane carries two home
+// atoms and evaluates both against the same staged neighbour with packed
+// FP32x2 arithmetic; lanes split each neighbour cell's atoms by stride ns.
+// The ns partial sums of an atom are then combined in split order, so each
+// atom's force is summed in an order fixed by the box state.  Lane l < nin
+// returns the totals of atom base + l.
+template <bool OBS>
+__device__ __forceinline__ void packed_forces(const BoxDev &B, const float4 *s_q, const int *s_start,
+                                              const int *s_cnt, int hx, int hy, int hz, int EY, int EZ,
+                                              int base, int nin, int lane, float &fx, float &fy,
+                                              float &fz, float &uu, float &ww)
+{
+    const int np = (nin + 1) >> 1;
+    const int ns = 32 / np;
+    const int pi = lane % np, g = lane / np;
+    const bool act = g < ns;
+    const int a0 = 2 * pi, a1 = min(2 * pi + 1, nin - 1);   // odd nin: the last pair repeats an atom
+    float2 FX = f2splat(0.f), FY = FX, FZ = FX, UU = FX, WW = FX;
+    if (act) {
+        const float4 q0 = s_q[base + a0], q1 = s_q[base + a1];
+        const float2 X = make_float2(q0.x, q1.x), Y = make_float2(q0.y, q1.y), Z = make_float2(q0.z, q1.z);
+        const unsigned rcb = __float_as_uint(B.rc2f);
+        const float2 c48 = f2splat(48.f), cm24 = f2splat(-24.f);
+        DSEA_CELL_UNROLL
+        for (int ox = -1; ox <= 1; ++ox)
+            DSEA_CELL_UNROLL
+            for (int oy = -1; oy <= 1; ++oy)
+                DSEA_CELL_UNROLL
+                for (int oz = -1; oz <= 1; ++oz) {
+                    const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+                    const int cs = s_start[kn], cn = s_cnt[kn];
+                    // home atoms in the neighbour cell's centred frame
+                    const float2 XS = f2sub(X, f2splat((float)ox * B.lcf[0]));
+                    const float2 YS = f2sub(Y, f2splat((float)oy * B.lcf[1]));
+                    const float2 ZS = f2sub(Z, f2splat((float)oz * B.lcf[2]));
+                    for (int t = g; t < cn; t += ns) {
+                        const float4 pj = s_q[cs + t];
+                        const float2 DX = f2sub(XS, f2splat(pj.x));
+                        const float2 DY = f2sub(YS, f2splat(pj.y));
+                        const float2 DZ = f2sub(ZS, f2splat(pj.z));
+                        const float2 R2 = f2fma(DZ, DZ, f2fma(DY, DY, f2mul(DX, DX)));
+                        const bool in0 = in_cutoff(R2.x, rcb), in1 = in_cutoff(R2.y, rcb);
+                        const float2 R2I = make_float2(rcp_approx(R2.x), rcp_approx(R2.y));
+                        const float2 A = f2mul(R2I, R2I);
+                        const float2 R6 = f2mul(A, R2I);
+                        // F_abs = 24 (2 r^-12 - r^-6) / r^2 = r^-8 (48 r^-6 - 24)
+                        float2 FS = f2mul(f2mul(A, A), f2fma(R6, c48, cm24));
+                        FS.x = in0 ? FS.x : 0.f;
+                        FS.y = in1 ? FS.y : 0.f;
+                        FX = f2fma(DX, FS, FX);
+                        FY = f2fma(DY, FS, FY);
+                        FZ = f2fma(DZ, FS, FZ);
+                        if (OBS) {
+                            // 4 (r^-12 - r^-6) + U_shift, and r_ij . F_ij
+                            float2 u = f2fma(f2mul(f2splat(4.f), R6), f2add(R6, f2splat(-1.f)),
+                                             f2splat(B.ushiftf));
+                            u.x = in0 ? u.x : 0.f;
+                            u.y = in1 ? u.y : 0.f;
+                            UU = f2add(UU, u);
+                            WW = f2fma(R2, FS, WW);
+                        }
+                    }
+                }
+    }
+    // combine the ns partials of each atom pair into lane pi, in split order
+    float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
+    for (int gg = 1; gg < ns; ++gg) {
+        const int src = pi + gg * np;   // < ns * np <= 32
+        SX.x += __shfl_sync(kFull, FX.x, src); SX.y += __shfl_sync(kFull, FX.y, src);
+        SY.x += __shfl_sync(kFull, FY.x, src); SY.y += __shfl_sync(kFull, FY.y, src);
+        SZ.x += __shfl_sync(kFull, FZ.x, src); SZ.y += __shfl_sync(kFull, FZ.y, src);
+        if (OBS) {
+            SU.x += __shfl_sync(kFull, UU.x, src); SU.y += __shfl_sync(kFull, UU.y, src);
+            SW.x += __shfl_sync(kFull, WW.x, src); SW.y += __shfl_sync(kFull, WW.y, src);
+        }
+    }
+    // atom l (l < nin) is half l & 1 of the pair held by lane l >> 1
+    const int from = (lane >> 1) < np ? (lane >> 1) : 0;
+    const bool hi = lane & 1;
+    float t0, t1;
+    t0 = __shfl_sync(kFull, SX.x, from); t1 = __shfl_sync(kFull, SX.y, from); fx = hi ? t1 : t0;
+    t0 = __shfl_sync(kFull, SY.x, from); t1 = __shfl_sync(kFull, SY.y, from); fy = hi ? t1 : t0;
+    t0 = __shfl_sync(kFull, SZ.x, from); t1 = __shfl_sync(kFull, SZ.y, from); fz = hi ? t1 : t0;
     if (OBS) {
-        const float u = fmaf(4.f * r6i, r6i - 1.f, ushift);  // 4 (r^-12 - r^-6) + U_shift
-        a.u += in ? u : 0.f;
-        a.w = fmaf(r2, fs, a.w);                              // r_ij . F_ij
+        t0 = __shfl_sync(kFull, SU.x, from); t1 = __shfl_sync(kFull, SU.y, from); uu = hi ? t1 : t0;
+        t0 = __shfl_sync(kFull, SW.x, from); t1 = __shfl_sync(kFull, SW.y, from); ww = hi ? t1 : t0;
     }
 }
 
 // One candidate pair in FP64 on absolute (periodically shifted) positions.
 template <bool OBS>
 __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, double xj, double yj,
-                                         double zj, double rc2, double ushift, Acc<double> &a)
+                                         double zj, double rc2, double ushift, Acc64 &a)
 {
     const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -146,9 +275,10 @@ __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, double
     }
 }
 
-// Reserve `1` slot per lane in cell `dest` of the next-step buffer; lanes
-// with the same destination share one compare-and-swap (warp aggregation).
-// Returns the slot index within the cell, or -1 for inactive lanes.
+// Reserve one slot per active lane in cell `dest` of the next-step buffer;
+// lanes with the same destination share one compare-and-swap (warp
+// aggregation).  Returns the slot index within the cell, or -1 for inactive
+// lanes.
 __device__ __forceinline__ int reserve_slot(unsigned long long *cnt, long long dest, bool active,
                                             unsigned tag, int lane, int *err)
 {
@@ -182,11 +312,9 @@ __device__ __forceinline__ int reserve_slot(unsigned long long *cnt, long long d
     return active ? base + rank : -1;
 }
 
-// Write one atom into slot `slot` of buffer `pn`.
-template <int PREC>
-__device__ __forceinline__ void store_atom(const BoxDev &B, int pn, long long slot, int aid,
-                                           long long cell, double x, double y, double z,
-                                           double vx, double vy, double vz, int cx, int cy, int cz)
+// Write one atom into slot `slot` of buffer `pn` (FP64 form).
+__device__ __forceinline__ void store_f64(const BoxDev &B, int pn, long long slot, int aid, double x,
+                                          double y, double z, double vx, double vy, double vz)
 {
     const long long S = B.n_slots;
     B.id[pn][slot] = aid;
@@ -196,14 +324,23 @@ __device__ __forceinline__ void store_atom(const BoxDev &B, int pn, long long sl
     B.v[pn][slot] = vx;
     B.v[pn][S + slot] = vy;
     B.v[pn][2 * S + slot] = vz;
-    if (PREC == 1) {
-        // FP32 coordinates relative to the centre of the atom's cell
-        const float qx = (float)(x - ((double)cx + 0.5) * B.lc[0]);
-        const float qy = (float)(y - ((double)cy + 0.5) * B.lc[1]);
-        const float qz = (float)(z - ((double)cz + 0.5) * B.lc[2]);
-        B.q[pn][slot] = make_float4(qx, qy, qz, __int_as_float(aid));
-    }
-    (void)cell;
+}
+
+// Write one atom into slot `slot` of buffer `pn` (mixed form): FP64 absolute
+// position, FP32 velocity, FP32 coordinates relative to its cell centre.
+__device__ __forceinline__ void store_mixed(const BoxDev &B, int pn, long long slot, int aid, double x,
+                                            double y, double z, float vx, float vy, float vz, float qx,
+                                            float qy, float qz)
+{
+    const long long S = B.n_slots;
+    B.id[pn][slot] = aid;
+    B.r[pn][slot] = x;
+    B.r[pn][S + slot] = y;
+    B.r[pn][2 * S + slot] = z;
+    B.vf[pn][slot] = vx;
+    B.vf[pn][S + slot] = vy;
+    B.vf[pn][2 * S + slot] = vz;
+    B.q[pn][slot] = make_float4(qx, qy, qz, __int_as_float(aid));
 }
 
 __device__ __forceinline__ double wrap_coord(double x, double L)
@@ -221,6 +358,32 @@ __device__ __forceinline__ int cell_of(double x, double inv_lc, int n)
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
+// Destination of a mixed-form atom along one axis.  The atom sat in home cell
+// `cg` with FP32 coordinate q relative to its centre and moved by d (FP32).
+// Returns the unwrapped destination cell and sets the new FP32 coordinate
+// relative to that cell's centre (from the FP64 position) and the wrapped
+// FP64 position.  ctab3 holds the FP64 centres of cells cg-1, cg, cg+1.
+__device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, const double *ctab3,
+                                         double lc, float inv_lcf, double L, int nc, float &qn)
+{
+    const int o = (int)floorf(fmaf(q + d, inv_lcf, 0.5f));   // cell offset, usually -1, 0 or 1
+    const int cu = cg + o;
+    const double ru = r + (double)d;                         // FP64 position update (unwrapped)
+    const double cen = (o >= -1 && o <= 1) ? ctab3[o + 1] : ((double)cu + 0.5) * lc;
+    qn = (float)(ru - cen);
+    int c = cu;
+    double rw = ru;
+    if (c < 0) {
+        c += nc;
+        rw += L;
+    } else if (c >= nc) {
+        c -= nc;
+        rw -= L;
+    }
+    r = rw;
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
 // The work unit (see file header).  s_abs: absolute step of the input state.
 template <int PREC, bool INTEGRATE, bool OBS>
 __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool first_step,
@@ -234,8 +397,8 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     int *s_start = reinterpret_cast<int *>(smem + Ly.start);
     int *s_gcell = reinterpret_cast<int *>(smem + Ly.gcell);
     int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
-    double *s_scr = reinterpret_cast<double *>(smem + Ly.scr);
     double *s_red = reinterpret_cast<double *>(smem + Ly.red);
+    int *s_ctr = reinterpret_cast<int *>(smem + Ly.ctr);
     float4 *s_q = reinterpret_cast<float4 *>(smem + Ly.atoms);
     double *s_x = reinterpret_cast<double *>(smem + Ly.atoms);
     double *s_y = s_x + B.smem_atoms;
@@ -251,6 +414,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     const int n_staged = (nx + 2) * EY * EZ;
 
     // 1. counts of the staged cells
+    if (tid == 0) *s_ctr = 0;
     for (int k = tid; k < n_staged; k += kThreads) {
         const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
         const int gx = wrap_index(x0 - 1 + lx, B.nc[0]);
@@ -331,42 +495,115 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     }
     __syncthreads();
 
-    // 4. forces, warp per home cell; lanes = (home atom, candidate split)
+    // 4./5. forces, then kick, drift and rebin, warp per home cell.  Without
+    // a reduction the home cells are handed out dynamically; with one, in a
+    // fixed order so that the unit's partial sums are reproducible.
     double red_u = 0.0, red_w = 0.0, red_k = 0.0;
     const int n_home = nx * ny * nz;
     const int pn = p ^ 1;
     const unsigned tag_next = tag + 1u;
     const double dt = B.dt;
     const double kick = first_step ? 0.5 * dt : dt;
-    for (int h = warp; h < n_home; h += kWarps) {
+    const float dtf = (float)dt;
+    int h = OBS ? warp : 0;
+    if (!OBS) {
+        if (lane == 0) h = atomicAdd(s_ctr, 1);
+        h = __shfl_sync(kFull, h, 0);
+    }
+    while (h < n_home) {
         const int hx = h / (ny * nz), hr = h - hx * ny * nz, hy = hr / nz, hz = hr - hy * nz;
         const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
         const int n_i = s_cnt[kh];
         const int hs = s_start[kh];
+        const int cg[3] = {x0 + hx, y0 + hy, z0 + hz};   // home cell (within the box)
+        double *ctab = reinterpret_cast<double *>(smem + Ly.ctab) + warp * 9;
+        if (PREC == 1) {
+            if (lane < 9) {
+                const int ax = lane / 3, o = lane - 3 * (lane / 3) - 1;
+                ctab[lane] = ((double)(cg[ax] + o) + 0.5) * B.lc[ax];
+            }
+            __syncwarp();
+        }
         for (int ib = 0; ib < n_i; ib += 32) {
             const int nin = min(32, n_i - ib);
             const int ns = 32 / nin;
             const int li = lane % nin, g = lane / nin;
             const bool act = g < ns;
             const int is = hs + ib + li;
-            Acc<float> a32 = {0.f, 0.f, 0.f, 0.f, 0.f};
-            Acc<double> a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
-            if (act) {
-                if (PREC == 1) {
-                    const float4 qi = s_q[is];
-                    for (int ox = -1; ox <= 1; ++ox)
-                        for (int oy = -1; oy <= 1; ++oy)
-                            for (int oz = -1; oz <= 1; ++oz) {
-                                const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
-                                const int cs = s_start[kn], cn = s_cnt[kn];
-                                // home atom in the neighbour cell's centred frame
-                                const float xs = qi.x - (float)ox * B.lcf[0];
-                                const float ys = qi.y - (float)oy * B.lcf[1];
-                                const float zs = qi.z - (float)oz * B.lcf[2];
-                                for (int t = g; t < cn; t += ns)
-                                    pair_f32<OBS>(xs, ys, zs, s_q[cs + t], B.rc2f, B.ushiftf, a32);
-                            }
-                } else {
+            const bool own = lane < nin;
+            long long slot = 0;
+            if (own) slot = s_slot[is];
+            if (PREC == 1) {
+                // prefetch this lane's atom position (FP64) and velocity (FP32)
+                char *pref = smem + Ly.scr + (size_t)warp * kPrefBytes;
+                double *pr = reinterpret_cast<double *>(pref);
+                float *pv = reinterpret_cast<float *>(pref + 32 * 3 * 8);
+                if (own) {
+                    for (int d = 0; d < 3; ++d) {
+                        cp_async8(pr + 3 * lane + d, B.r[p] + d * S + slot);
+                        cp_async4(pv + 3 * lane + d, B.vf[p] + d * S + slot);
+                    }
+                }
+                float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
+                packed_forces<OBS>(B, s_q, s_start, s_cnt, hx, hy, hz, EY, EZ, hs + ib, nin, lane, fx,
+                                   fy, fz, uu, ww);
+                cp_async_wait_all();
+                __syncwarp();
+                int aid = 0;
+                double rr[3] = {0.0, 0.0, 0.0};
+                float vv[3] = {0.f, 0.f, 0.f};
+                float4 qo = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (own) {
+                    qo = s_q[is];
+                    aid = __float_as_int(qo.w);
+                    for (int d = 0; d < 3; ++d) {
+                        rr[d] = pr[3 * lane + d];
+                        vv[d] = pv[3 * lane + d];
+                    }
+                    if (OBS) {
+                        // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
+                        const float hk = first_step ? 0.f : 0.5f * dtf;
+                        const float sx = fmaf(hk, fx, vv[0]), sy = fmaf(hk, fy, vv[1]), sz = fmaf(hk, fz, vv[2]);
+                        red_u += 0.5 * (double)uu;
+                        red_w += 0.5 * (double)ww;
+                        red_k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+                        if (!INTEGRATE) {
+                            const long long o = 3LL * aid;
+                            B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
+                            B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
+                            B.out_r[o] = rr[0]; B.out_r[o + 1] = rr[1]; B.out_r[o + 2] = rr[2];
+                        }
+                    }
+                }
+                __syncwarp();   // the prefetch area is reused by the next chunk
+                if (INTEGRATE) {
+                    long long dest = 0;
+                    float qn[3] = {0.f, 0.f, 0.f};
+                    if (own) {
+                        const float kf = first_step ? 0.5f * dtf : dtf;
+                        vv[0] = fmaf(kf, fx, vv[0]);   // v(t + dt/2) = v(t - dt/2) + F dt
+                        vv[1] = fmaf(kf, fy, vv[1]);
+                        vv[2] = fmaf(kf, fz, vv[2]);
+                        const float q3[3] = {qo.x, qo.y, qo.z};
+                        int c3[3];
+                        for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
+                            c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], ctab + 3 * d, B.lc[d],
+                                              1.0f / B.lcf[d], B.L[d], B.nc[d], qn[d]);
+                        const int dj = c3[0] / B.cps - j;
+                        const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
+                        if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
+                        dest = ((long long)c3[0] * B.nc[1] + c3[1]) * B.nc[2] + c3[2];
+                    }
+                    const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
+                    if (own) {
+                        if (k >= B.cap) set_error(B.err, kErrCapacity);
+                        else store_mixed(B, pn, dest * B.cap + k, aid, rr[0], rr[1], rr[2], vv[0], vv[1],
+                                         vv[2], qn[0], qn[1], qn[2]);
+                    }
+                }
+            } else {
+                Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
+                if (act) {
                     const double xi = s_x[is], yi = s_y[is], zi = s_z[is];
                     for (int ox = -1; ox <= 1; ++ox)
                         for (int oy = -1; oy <= 1; ++oy)
@@ -378,30 +615,10 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                                                   B.rc2, B.ushift, a64);
                             }
                 }
-            }
-            // combine the ns partial sums of each home atom in split order
-            double fx, fy, fz, uu, ww;
-            if (PREC == 1) {
-                fx = a32.fx; fy = a32.fy; fz = a32.fz; uu = a32.u; ww = a32.w;
-            } else {
-                fx = a64.fx; fy = a64.fy; fz = a64.fz; uu = a64.u; ww = a64.w;
-            }
-            if (ns > 1) {
-                double *scr = s_scr + warp * 32 * 5;
-                if (PREC == 1) {
-                    float *sf = reinterpret_cast<float *>(scr);
-                    sf[lane * 5 + 0] = a32.fx; sf[lane * 5 + 1] = a32.fy; sf[lane * 5 + 2] = a32.fz;
-                    sf[lane * 5 + 3] = a32.u;  sf[lane * 5 + 4] = a32.w;
-                    __syncwarp();
-                    if (g == 0) {
-                        float bx = a32.fx, by = a32.fy, bz = a32.fz, bu = a32.u, bw = a32.w;
-                        for (int gg = 1; gg < ns; ++gg) {
-                            const int o = (li + gg * nin) * 5;
-                            bx += sf[o]; by += sf[o + 1]; bz += sf[o + 2]; bu += sf[o + 3]; bw += sf[o + 4];
-                        }
-                        fx = bx; fy = by; fz = bz; uu = bu; ww = bw;
-                    }
-                } else {
+                // combine the ns partial sums of each home atom in split order
+                double fx = a64.fx, fy = a64.fy, fz = a64.fz, uu = a64.u, ww = a64.w;
+                if (ns > 1) {
+                    double *scr = reinterpret_cast<double *>(smem + Ly.scr) + warp * 32 * 5;
                     scr[lane * 5 + 0] = a64.fx; scr[lane * 5 + 1] = a64.fy; scr[lane * 5 + 2] = a64.fz;
                     scr[lane * 5 + 3] = a64.u;  scr[lane * 5 + 4] = a64.w;
                     __syncwarp();
@@ -411,67 +628,63 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                             fx += scr[o]; fy += scr[o + 1]; fz += scr[o + 2]; uu += scr[o + 3]; ww += scr[o + 4];
                         }
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
-            }
-            // 5. kick, drift, rebin (lanes holding a home atom: lane < nin)
-            const bool own = lane < nin;
-            int aid = 0;
-            long long slot = 0;
-            double rx = 0, ry = 0, rz = 0, vx = 0, vy = 0, vz = 0;
-            if (own) {
-                slot = s_slot[is];
-                aid = (PREC == 1) ? __float_as_int(s_q[is].w) : s_id[is];
-                rx = __ldcg(B.r[p] + slot);
-                ry = __ldcg(B.r[p] + S + slot);
-                rz = __ldcg(B.r[p] + 2 * S + slot);
-                vx = __ldcg(B.v[p] + slot);
-                vy = __ldcg(B.v[p] + S + slot);
-                vz = __ldcg(B.v[p] + 2 * S + slot);
-                if (OBS) {
-                    // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
-                    const double hk = first_step ? 0.0 : 0.5 * dt;
-                    const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
-                    red_u += 0.5 * uu;
-                    red_w += 0.5 * ww;
-                    red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
-                    if (!INTEGRATE) {
-                        const long long o = 3LL * aid;
-                        B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
-                        B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
-                        B.out_r[o] = rx; B.out_r[o + 1] = ry; B.out_r[o + 2] = rz;
+                int aid = 0;
+                double rx = 0, ry = 0, rz = 0, vx = 0, vy = 0, vz = 0;
+                if (own) {
+                    aid = s_id[is];
+                    rx = __ldcg(B.r[p] + slot);
+                    ry = __ldcg(B.r[p] + S + slot);
+                    rz = __ldcg(B.r[p] + 2 * S + slot);
+                    vx = __ldcg(B.v[p] + slot);
+                    vy = __ldcg(B.v[p] + S + slot);
+                    vz = __ldcg(B.v[p] + 2 * S + slot);
+                    if (OBS) {
+                        const double hk = first_step ? 0.0 : 0.5 * dt;
+                        const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
+                        red_u += 0.5 * uu;
+                        red_w += 0.5 * ww;
+                        red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
+                        if (!INTEGRATE) {
+                            const long long o = 3LL * aid;
+                            B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
+                            B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
+                            B.out_r[o] = rx; B.out_r[o + 1] = ry; B.out_r[o + 2] = rz;
+                        }
                     }
                 }
-            }
-            if (INTEGRATE) {
-                long long dest = 0;
-                int cx = 0, cy = 0, cz = 0;
-                if (own) {
-                    vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
-                    vy += kick * fy;
-                    vz += kick * fz;
-                    rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
-                    ry = wrap_coord(ry + vy * dt, B.L[1]);
-                    rz = wrap_coord(rz + vz * dt, B.L[2]);
-                    cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
-                    cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
-                    cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
-                    const int dj = cx / B.cps - j;
-                    const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
-                    if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
-                    dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
-                }
-                const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
-                if (own) {
-                    if (k >= B.cap) {
-                        set_error(B.err, kErrCapacity);
-                    } else {
-                        store_atom<PREC>(B, pn, dest * B.cap + k, aid, dest, rx, ry, rz, vx, vy,
-                                         vz, cx, cy, cz);
+                if (INTEGRATE) {
+                    long long dest = 0;
+                    if (own) {
+                        vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
+                        vy += kick * fy;
+                        vz += kick * fz;
+                        rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
+                        ry = wrap_coord(ry + vy * dt, B.L[1]);
+                        rz = wrap_coord(rz + vz * dt, B.L[2]);
+                        const int cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
+                        const int cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
+                        const int cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
+                        const int dj = cx / B.cps - j;
+                        const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
+                        if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
+                        dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
+                    }
+                    const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
+                    if (own) {
+                        if (k >= B.cap) set_error(B.err, kErrCapacity);
+                        else store_f64(B, pn, dest * B.cap + k, aid, rx, ry, rz, vx, vy, vz);
                     }
                 }
             }
             __syncwarp();
+        }
+        if (OBS) {
+            h += kWarps;
+        } else {
+            if (lane == 0) h = atomicAdd(s_ctr, 1);
+            h = __shfl_sync(kFull, h, 0);
         }
     }
     if (OBS) {
@@ -537,8 +750,18 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
         }
         const int k = reserve_slot(B.cnt[p], dest, own, tag, lane, B.err);
         if (own) {
-            if (k >= B.cap) set_error(B.err, kErrCapacity);
-            else store_atom<PREC>(B, p, dest * B.cap + k, (int)i, dest, x, y, z, vx, vy, vz, cx, cy, cz);
+            if (k >= B.cap) {
+                set_error(B.err, kErrCapacity);
+            } else if (PREC == 1) {
+                // FP32 coordinates relative to the centre of the atom's cell
+                const float qx = (float)(x - ((double)cx + 0.5) * B.lc[0]);
+                const float qy = (float)(y - ((double)cy + 0.5) * B.lc[1]);
+                const float qz = (float)(z - ((double)cz + 0.5) * B.lc[2]);
+                store_mixed(B, p, dest * B.cap + k, (int)i, x, y, z, (float)vx, (float)vy, (float)vz, qx,
+                            qy, qz);
+            } else {
+                store_f64(B, p, dest * B.cap + k, (int)i, x, y, z, vx, vy, vz);
+            }
         }
     }
 }
@@ -591,8 +814,11 @@ __global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int 
 // by about five slices (the time-skewed cyclic order of Sec. 3.1 / Table 1).
 // A CTA only waits on tickets smaller than its own, all of which were taken
 // by running CTAs, so the ring always progresses.
+#ifndef DSEA_RING_MIN_BLOCKS
+#define DSEA_RING_MIN_BLOCKS 4   // CTAs per SM the register allocation must allow
+#endif
 template <int PREC>
-__global__ void __launch_bounds__(kThreads) k_ring(RingPlan plan)
+__global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring(RingPlan plan)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;

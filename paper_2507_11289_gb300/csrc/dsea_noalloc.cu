@@ -83,7 +83,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     const size_t o_cnt = take(sizeof(unsigned long long) * hb.n_cells);
     const size_t o_id = take(sizeof(int) * hb.n_slots);
     const size_t o_r = take(sizeof(double) * 3 * hb.n_slots);
-    const size_t o_v = take(sizeof(double) * 3 * hb.n_slots);
+    const size_t o_v = take((precision == DSEA_MIXED ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots);
     const size_t o_q = precision == DSEA_MIXED ? take(sizeof(float4) * hb.n_slots) : 0;
     const size_t o_obs = take(sizeof(double) * 3 * (size_t)units);
     const size_t o_outr = take(sizeof(double) * n3);
@@ -99,7 +99,8 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
         hb.cnt[q] = reinterpret_cast<unsigned long long *>(base + o_cnt);
         hb.id[q] = reinterpret_cast<int *>(base + o_id);
         hb.r[q] = reinterpret_cast<double *>(base + o_r);
-        hb.v[q] = reinterpret_cast<double *>(base + o_v);
+        hb.v[q] = precision == DSEA_MIXED ? nullptr : reinterpret_cast<double *>(base + o_v);
+        hb.vf[q] = precision == DSEA_MIXED ? reinterpret_cast<float *>(base + o_v) : nullptr;
         hb.q[q] = precision == DSEA_MIXED ? reinterpret_cast<float4 *>(base + o_q) : nullptr;
     }
     hb.unit_obs = reinterpret_cast<double *>(base + o_obs);

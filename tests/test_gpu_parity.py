@@ -216,3 +216,28 @@ def test_full_1m_box_sampled_atoms(precision):
     tol = 1e-12 if precision == dsea.FP64 else 2e-6
     assert rms(Fg[idx] - Fo) <= tol * rms(Fo)
     assert np.abs(Fg.sum(0)).max() <= (1e-9 if precision == dsea.FP64 else 1e-3) * rms(Fg) * np.sqrt(len(pos))
+
+
+def test_full_67m_box_sampled_atoms():
+    """67,108,864-atom box (256^3 fcc cells, rho 0.8), 175 slices, mixed form
+    as the benchmark runs it: forces at 512 sampled atoms against the oracle
+    after one ring step from a jittered lattice, plus Newton's third law."""
+    spec = inputs.FLUID_67M
+    pos, vel, box = spec.state()
+    pos = inputs.jitter(pos, box, 0.1, 23)
+    rng = np.random.Generator(np.random.PCG64(6))
+    idx = np.sort(rng.choice(len(pos), 512, replace=False))
+    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+        info = b.info()
+        assert info["n_slices"] == 175 and info["cells"] == [175, 175, 175]
+        Fg = b.forces()
+        b.advance(1)
+        r1 = b.positions()
+        F1 = b.forces()
+    Fo, _, _ = oracle.forces_subset(pos, box, idx, RC)
+    assert rms(Fg[idx] - Fo) <= 2e-6 * rms(Fo)
+    assert np.abs(Fg.sum(0)).max() <= 1e-3 * rms(Fg) * np.sqrt(len(pos))
+    del Fg
+    # one step later: the sampled atoms' forces at the GPU's new positions
+    F1o, _, _ = oracle.forces_subset(r1, box, idx, RC)
+    assert rms(F1[idx] - F1o) <= 2e-6 * rms(F1o)
