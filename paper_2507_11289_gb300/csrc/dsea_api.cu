@@ -98,10 +98,12 @@ bool apply_tile(BoxDev &hb, double mean_cap, int ty, int tz)
     hb.units_per_slice = hb.tiles_y * hb.tiles_z;
     hb.staged_cells = (hb.cps + 2) * (ty + 2) * (tz + 2);
     if (hb.staged_cells > dsea::kMaxStagedCells) return false;
-    // room for the expected stage plus a quarter, never more than every slot
-    const double expect = hb.staged_cells * mean_cap * 1.25 + 64.0;
+    // room for the expected stage plus a quarter (plus the FP64 form's padding
+    // of each cell to 4 slots), never more than every slot; a multiple of 4
+    const double pad = hb.precision == DSEA_FP64 ? 3.0 * hb.staged_cells : 0.0;
+    const double expect = hb.staged_cells * mean_cap * 1.25 + 64.0 + pad;
     const double worst = (double)hb.staged_cells * hb.cap;
-    hb.smem_atoms = (int)std::ceil(std::min(expect, worst));
+    hb.smem_atoms = ((int)std::ceil(std::min(expect, worst)) + 3) & ~3;
     return dsea::unit_smem_bytes(hb.precision, hb.staged_cells, hb.smem_atoms) <=
            dsea::max_unit_smem_bytes();
 }
@@ -272,8 +274,9 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     int cap = p.cell_capacity;
     if (cap <= 0) {
         cap = (int)std::ceil(mean_cap + 6.0 * std::sqrt(mean_cap) + 6.0);
-        cap = std::max(8, (cap + 3) / 4 * 4);
+        cap = std::max(8, cap);
     }
+    cap = (cap + 3) / 4 * 4;   // slot ranges start 16-byte aligned in every per-slot array
     hb.cap = cap;
     hb.n_slots = hb.n_cells * cap;
     if (hb.n_slots >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;

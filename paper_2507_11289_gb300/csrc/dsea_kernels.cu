@@ -61,17 +61,13 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Asynchronous global -> shared copies (L2 only, so data other CTAs wrote
-// during the same launch is seen).
-__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+// Asynchronous 16-byte global -> shared copy that bypasses L1 (.cg), so data
+// other CTAs wrote earlier in the same persistent launch is always seen (L1
+// is not kept coherent with other SMs' writes).  Both addresses 16-B aligned.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all()
 {
@@ -164,6 +160,60 @@ __device__ __forceinline__ bool in_cutoff(float r2, unsigned rc2_bits)
     return (__float_as_uint(r2) - 1u) < rc2_bits;
 }
 
+// 1.0f if a <= b, else 0.0f (one instruction; multiplies a force to zero
+// beyond the cutoff).
+__device__ __forceinline__ float le_mask(float a, float b)
+{
+    float d;
+    asm("set.le.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Accumulators of the two home atoms a lane carries (packed halves).
+struct Acc2 {
+    float2 fx, fy, fz, u, w;
+};
+
+// Two home atoms (XS, YS, ZS: already in the neighbour cell's frame) against
+// one staged neighbour.  EXACT: the cutoff test also excludes r2 == 0 (the
+// atom itself; needed in the home cell) and masks the energy terms; otherwise
+// the force is masked by multiplying with the 0/1 cutoff mask, which gives
+// the same bits for every pair of distinct atoms.
+template <bool EXACT, bool OBS>
+__device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const float2 ZS, const float4 pj,
+                                      float rc2f, unsigned rcb, float ushiftf, Acc2 &a)
+{
+    const float2 DX = f2sub(XS, f2splat(pj.x));
+    const float2 DY = f2sub(YS, f2splat(pj.y));
+    const float2 DZ = f2sub(ZS, f2splat(pj.z));
+    const float2 R2 = f2fma(DZ, DZ, f2fma(DY, DY, f2mul(DX, DX)));
+    const float2 R2I = make_float2(rcp_approx(R2.x), rcp_approx(R2.y));
+    const float2 A = f2mul(R2I, R2I);
+    const float2 R6 = f2mul(A, R2I);
+    // F_abs = 24 (2 r^-12 - r^-6) / r^2 = r^-8 (48 r^-6 - 24)
+    float2 FS = f2mul(f2mul(A, A), f2fma(R6, f2splat(48.f), f2splat(-24.f)));
+    bool in0 = true, in1 = true;
+    if (EXACT) {
+        in0 = in_cutoff(R2.x, rcb);
+        in1 = in_cutoff(R2.y, rcb);
+        FS.x = in0 ? FS.x : 0.f;
+        FS.y = in1 ? FS.y : 0.f;
+    } else {
+        FS = f2mul(FS, make_float2(le_mask(R2.x, rc2f), le_mask(R2.y, rc2f)));
+    }
+    a.fx = f2fma(DX, FS, a.fx);
+    a.fy = f2fma(DY, FS, a.fy);
+    a.fz = f2fma(DZ, FS, a.fz);
+    if (OBS) {
+        // 4 (r^-12 - r^-6) + U_shift, and r_ij . F_ij
+        float2 u = f2fma(f2mul(f2splat(4.f), R6), f2add(R6, f2splat(-1.f)), f2splat(ushiftf));
+        u.x = in0 ? u.x : 0.f;
+        u.y = in1 ? u.y : 0.f;
+        a.u = f2add(a.u, u);
+        a.w = f2fma(R2, FS, a.w);
+    }
+}
+
 // Mixed-form forces on the atoms of one home cell chunk (nin <= 32 atoms
 // starting at staged index `base`), warp-wide.  Each lane carries two home
 // atoms and evaluates both against the same staged neighbour with packed
@@ -182,12 +232,12 @@ __device__ __forceinline__ void packed_forces(const BoxDev &B, const float4 *s_q
     const int pi = lane % np, g = lane / np;
     const bool act = g < ns;
     const int a0 = 2 * pi, a1 = min(2 * pi + 1, nin - 1);   // odd nin: the last pair repeats an atom
-    float2 FX = f2splat(0.f), FY = FX, FZ = FX, UU = FX, WW = FX;
+    Acc2 acc = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)};
     if (act) {
         const float4 q0 = s_q[base + a0], q1 = s_q[base + a1];
         const float2 X = make_float2(q0.x, q1.x), Y = make_float2(q0.y, q1.y), Z = make_float2(q0.z, q1.z);
         const unsigned rcb = __float_as_uint(B.rc2f);
-        const float2 c48 = f2splat(48.f), cm24 = f2splat(-24.f);
+        const float rc2f = B.rc2f, ush = B.ushiftf;
         DSEA_CELL_UNROLL
         for (int ox = -1; ox <= 1; ++ox)
             DSEA_CELL_UNROLL
@@ -200,35 +250,22 @@ __device__ __forceinline__ void packed_forces(const BoxDev &B, const float4 *s_q
                     const float2 XS = f2sub(X, f2splat((float)ox * B.lcf[0]));
                     const float2 YS = f2sub(Y, f2splat((float)oy * B.lcf[1]));
                     const float2 ZS = f2sub(Z, f2splat((float)oz * B.lcf[2]));
-                    for (int t = g; t < cn; t += ns) {
-                        const float4 pj = s_q[cs + t];
-                        const float2 DX = f2sub(XS, f2splat(pj.x));
-                        const float2 DY = f2sub(YS, f2splat(pj.y));
-                        const float2 DZ = f2sub(ZS, f2splat(pj.z));
-                        const float2 R2 = f2fma(DZ, DZ, f2fma(DY, DY, f2mul(DX, DX)));
-                        const bool in0 = in_cutoff(R2.x, rcb), in1 = in_cutoff(R2.y, rcb);
-                        const float2 R2I = make_float2(rcp_approx(R2.x), rcp_approx(R2.y));
-                        const float2 A = f2mul(R2I, R2I);
-                        const float2 R6 = f2mul(A, R2I);
-                        // F_abs = 24 (2 r^-12 - r^-6) / r^2 = r^-8 (48 r^-6 - 24)
-                        float2 FS = f2mul(f2mul(A, A), f2fma(R6, c48, cm24));
-                        FS.x = in0 ? FS.x : 0.f;
-                        FS.y = in1 ? FS.y : 0.f;
-                        FX = f2fma(DX, FS, FX);
-                        FY = f2fma(DY, FS, FY);
-                        FZ = f2fma(DZ, FS, FZ);
-                        if (OBS) {
-                            // 4 (r^-12 - r^-6) + U_shift, and r_ij . F_ij
-                            float2 u = f2fma(f2mul(f2splat(4.f), R6), f2add(R6, f2splat(-1.f)),
-                                             f2splat(B.ushiftf));
-                            u.x = in0 ? u.x : 0.f;
-                            u.y = in1 ? u.y : 0.f;
-                            UU = f2add(UU, u);
-                            WW = f2fma(R2, FS, WW);
+                    const float4 *qc = s_q + cs;
+                    int t = g;
+                    if (!OBS && (ox | oy | oz) != 0) {
+                        // no self pair here: two independent candidates per iteration
+                        for (; t + ns < cn; t += 2 * ns) {
+                            const float4 pj0 = qc[t], pj1 = qc[t + ns];
+                            pair2<false, false>(XS, YS, ZS, pj0, rc2f, rcb, ush, acc);
+                            pair2<false, false>(XS, YS, ZS, pj1, rc2f, rcb, ush, acc);
                         }
+                        if (t < cn) pair2<false, false>(XS, YS, ZS, qc[t], rc2f, rcb, ush, acc);
+                    } else {
+                        for (; t < cn; t += ns) pair2<true, OBS>(XS, YS, ZS, qc[t], rc2f, rcb, ush, acc);
                     }
                 }
     }
+    const float2 FX = acc.fx, FY = acc.fy, FZ = acc.fz, UU = acc.u, WW = acc.w;
     // combine the ns partials of each atom pair into lane pi, in split order
     float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
     for (int gg = 1; gg < ns; ++gg) {
@@ -431,12 +468,14 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         s_gcell[k] = gc;
     }
     __syncthreads();
-    // 2. exclusive scan (warp 0, contiguous chunks per lane)
+    // 2. exclusive scan (warp 0, contiguous chunks per lane).  FP64 cells
+    // start on a multiple of 4 atoms so that their 8- and 4-byte arrays can
+    // be staged in 16-byte copies.
     if (warp == 0) {
         const int per = (n_staged + 31) / 32;
         const int b = lane * per, e = min(b + per, n_staged);
         int sum = 0;
-        for (int k = b; k < e; ++k) sum += s_cnt[k];
+        for (int k = b; k < e; ++k) sum += PREC == 0 ? (s_cnt[k] + 3) & ~3 : s_cnt[k];
         int incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(kFull, incl, o);
@@ -445,7 +484,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         int run = incl - sum;
         for (int k = b; k < e; ++k) {
             s_start[k] = run;
-            run += s_cnt[k];
+            run += PREC == 0 ? (s_cnt[k] + 3) & ~3 : s_cnt[k];
         }
         if (lane == 31) s_start[n_staged] = incl;
     }
@@ -454,8 +493,133 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         if (tid == 0) set_error(B.err, kErrCapacity);
         return;
     }
-    // 3. stage atoms, each cell sorted by atom id (warp per cell)
+    // 3. stage atoms, each cell sorted by atom id.  3a: every warp issues
+    // asynchronous 16-byte copies of its cells' slots in slot order and moves
+    // on without waiting; 3b: after one wait and barrier, each cell is sorted
+    // in place by atom id (warp per cell, lanes rank their atoms by shuffles).
     const long long S = B.n_slots;
+    if (B.cap <= 128) {
+        for (int k = warp; k < n_staged; k += kWarps) {
+            const int c = s_cnt[k];
+            if (c == 0) continue;
+            const long long base = (long long)s_gcell[k] * B.cap;
+            const int st = s_start[k];
+            if (PREC == 1) {
+                for (int a = lane; a < c; a += 32) cp_async16(s_q + st + a, B.q[p] + base + a);
+            } else {
+                const int n2 = (c + 1) >> 1, n4 = (c + 3) >> 2;   // 16-byte chunks
+                for (int q = lane; q < 3 * n2 + n4; q += 32) {
+                    if (q < 3 * n2) {
+                        const int d = q / n2, ch = q - d * n2;
+                        double *dst = (d == 0 ? s_x : (d == 1 ? s_y : s_z)) + st + 2 * ch;
+                        cp_async16(dst, B.r[p] + d * S + base + 2 * ch);
+                    } else {
+                        const int ch = q - 3 * n2;
+                        cp_async16(s_id + st + 4 * ch, B.id[p] + base + 4 * ch);
+                    }
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int k = warp; k < n_staged; k += kWarps) {
+            const int c = s_cnt[k];
+            if (c == 0) continue;
+            const long long base = (long long)s_gcell[k] * B.cap;
+            const int st = s_start[k];
+            const int nm = (c + 31) >> 5;   // atoms per lane (<= 4)
+            double shx = 0.0, shy = 0.0, shz = 0.0;
+            if (PREC == 0) {   // periodic image shift of this staged cell
+                const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
+                const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
+                shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
+                shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
+                shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
+            }
+            if (nm == 1) {   // the common case: one atom per lane
+                int id0 = 0x7fffffff;
+                float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
+                double x0v = 0.0, y0v = 0.0, z0v = 0.0;
+                if (lane < c) {
+                    if (PREC == 1) {
+                        q0 = s_q[st + lane];
+                        id0 = __float_as_int(q0.w);
+                    } else {
+                        x0v = s_x[st + lane] + shx;
+                        y0v = s_y[st + lane] + shy;
+                        z0v = s_z[st + lane] + shz;
+                        id0 = s_id[st + lane];
+                    }
+                }
+                int rank = 0;
+                for (int t = 0; t < c; ++t) rank += (__shfl_sync(kFull, id0, t) < id0) ? 1 : 0;
+                __syncwarp();   // every lane has read the cell before any writes
+                if (lane < c) {
+                    const int dst = st + rank;
+                    s_slot[dst] = (int)(base + lane);
+                    if (PREC == 1) {
+                        s_q[dst] = q0;
+                    } else {
+                        s_x[dst] = x0v;
+                        s_y[dst] = y0v;
+                        s_z[dst] = z0v;
+                        s_id[dst] = id0;
+                    }
+                }
+                continue;
+            }
+            int idm[4];
+            float4 qm[4];
+            double xm[4], ym[4], zm[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int a = lane + 32 * m;
+                idm[m] = 0x7fffffff;
+                if (m < nm && a < c) {
+                    if (PREC == 1) {
+                        qm[m] = s_q[st + a];
+                        idm[m] = __float_as_int(qm[m].w);
+                    } else {
+                        xm[m] = s_x[st + a] + shx;
+                        ym[m] = s_y[st + a] + shy;
+                        zm[m] = s_z[st + a] + shz;
+                        idm[m] = s_id[st + a];
+                    }
+                }
+            }
+            int rk[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int mb = 0; mb < 4; ++mb) {
+                if (mb < nm) {
+                    const int lim = min(32, c - 32 * mb);
+                    for (int t = 0; t < lim; ++t) {
+                        const int o = __shfl_sync(kFull, idm[mb], t);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (m < nm) rk[m] += (o < idm[m]) ? 1 : 0;
+                    }
+                }
+            }
+            __syncwarp();   // every lane has read the cell before any writes
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int a = lane + 32 * m;
+                if (m < nm && a < c) {
+                    const int dst = st + rk[m];
+                    s_slot[dst] = (int)(base + a);
+                    if (PREC == 1) {
+                        s_q[dst] = qm[m];
+                    } else {
+                        s_x[dst] = xm[m];
+                        s_y[dst] = ym[m];
+                        s_z[dst] = zm[m];
+                        s_id[dst] = idm[m];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    } else {
     for (int k = warp; k < n_staged; k += kWarps) {
         const int c = s_cnt[k];
         if (c == 0) continue;
@@ -494,6 +658,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         }
     }
     __syncthreads();
+    }   // cells of more than 128 slots: the loads above wait per cell
 
     // 4./5. forces, then kick, drift and rebin, warp per home cell.  Without
     // a reduction the home cells are handed out dynamically; with one, in a
@@ -534,14 +699,24 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
             long long slot = 0;
             if (own) slot = s_slot[is];
             if (PREC == 1) {
-                // prefetch this lane's atom position (FP64) and velocity (FP32)
+                // prefetch the home cell's positions (FP64) and velocities (FP32)
+                // in slot order, 16-byte copies, while the forces are computed
+                // (cells of up to 32 atoms; larger ones are read after)
                 char *pref = smem + Ly.scr + (size_t)warp * kPrefBytes;
-                double *pr = reinterpret_cast<double *>(pref);
-                float *pv = reinterpret_cast<float *>(pref + 32 * 3 * 8);
-                if (own) {
-                    for (int d = 0; d < 3; ++d) {
-                        cp_async8(pr + 3 * lane + d, B.r[p] + d * S + slot);
-                        cp_async4(pv + 3 * lane + d, B.vf[p] + d * S + slot);
+                double *pr = reinterpret_cast<double *>(pref);          // [3][32]
+                float *pv = reinterpret_cast<float *>(pref + 32 * 3 * 8);  // [3][32]
+                const long long hbase = (long long)s_gcell[kh] * B.cap;
+                const bool pf = n_i <= 32;
+                if (pf) {
+                    const int n2 = (n_i + 1) >> 1, n4 = (n_i + 3) >> 2;
+                    for (int q = lane; q < 3 * (n2 + n4); q += 32) {
+                        if (q < 3 * n2) {
+                            const int d = q / n2, ch = q - d * n2;
+                            cp_async16(pr + 32 * d + 2 * ch, B.r[p] + d * S + hbase + 2 * ch);
+                        } else {
+                            const int q2 = q - 3 * n2, d = q2 / n4, ch = q2 - d * n4;
+                            cp_async16(pv + 32 * d + 4 * ch, B.vf[p] + d * S + hbase + 4 * ch);
+                        }
                     }
                 }
                 float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
@@ -557,8 +732,9 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                     qo = s_q[is];
                     aid = __float_as_int(qo.w);
                     for (int d = 0; d < 3; ++d) {
-                        rr[d] = pr[3 * lane + d];
-                        vv[d] = pv[3 * lane + d];
+                        const int a = (int)(slot - hbase);
+                        rr[d] = pf ? pr[32 * d + a] : __ldcg(B.r[p] + d * S + slot);
+                        vv[d] = pf ? pv[32 * d + a] : __ldcg(B.vf[p] + d * S + slot);
                     }
                     if (OBS) {
                         // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
