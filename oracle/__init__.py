@@ -46,21 +46,41 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def build_variant(out_path: str, defines=()) -> str:
+    """Compile lj_oracle.c with extra -D defines into out_path (the mutation
+    tests plant deliberate mistakes this way; the oracle itself never does)."""
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", *[f"-D{d}" for d in defines], "-o", out_path, _SRC, "-lm"])
+    return out_path
+
+
+def use_library(path):
+    """Point the wrappers at another build of lj_oracle.c (None: the default
+    build).  Returns the previously loaded library handle."""
+    global _lib
+    prev = _lib
+    _lib = None if path is None else _configure(ctypes.CDLL(path))
+    return prev
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
-        lib.oracle_pair.argtypes = [d, d, p, p]
-        lib.oracle_forces_brute.argtypes = [i64, p, p, d, p, p, p]
-        lib.oracle_forces_cells.argtypes = [i64, p, p, d, p, p, p]
-        lib.oracle_forces_subset.argtypes = [i64, p, p, d, i64, p, p, p, p]
-        lib.oracle_run.argtypes = [i64, p, p, p, d, d, i64, ctypes.c_int, p, p]
-        for f in (lib.oracle_pair, lib.oracle_forces_brute, lib.oracle_forces_cells,
-                  lib.oracle_forces_subset, lib.oracle_run):
-            f.restype = ctypes.c_int
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
+    lib.oracle_pair.argtypes = [d, d, p, p]
+    lib.oracle_forces_brute.argtypes = [i64, p, p, d, p, p, p]
+    lib.oracle_forces_cells.argtypes = [i64, p, p, d, p, p, p]
+    lib.oracle_forces_subset.argtypes = [i64, p, p, d, i64, p, p, p, p]
+    lib.oracle_run.argtypes = [i64, p, p, p, d, d, i64, ctypes.c_int, p, p]
+    for f in (lib.oracle_pair, lib.oracle_forces_brute, lib.oracle_forces_cells,
+              lib.oracle_forces_subset, lib.oracle_run):
+        f.restype = ctypes.c_int
+    return lib
 
 
 def _ptr(a: np.ndarray):

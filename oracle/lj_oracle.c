@@ -35,6 +35,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Planted-mistake builds for the mutation tests (tests/test_oracle_mutants.py):
+ * 0 = the oracle as written; any other value compiles one deliberate error so the
+ * tests can show that the pins detect it.  Never set outside those tests. */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
 #define ORACLE_OK 0
 #define ORACLE_ERR_ARG -1
 #define ORACLE_ERR_CELLS -2
@@ -57,14 +64,14 @@ static void lj_pair_terms(double r2, double ushift, double *fabs_out, double *u_
     double r2i = 1.0 / r2;
     double r6i = r2i * r2i * r2i;    /* sigma^6 / r^6  */
     double r12i = r6i * r6i;         /* sigma^12 / r^12 */
-    *fabs_out = 24.0 * (2.0 * r12i - r6i) * r2i;
-    *u_out = 4.0 * (r12i - r6i) + ushift;
+    *fabs_out = 24.0 * ((ORACLE_MUTANT == 1 ? 1.0 : 2.0) * r12i - r6i) * r2i;
+    *u_out = 4.0 * (r12i - r6i) + (ORACLE_MUTANT == 2 ? -ushift : ushift);
 }
 
 /* Minimum-image component of a separation along a periodic axis of length L. */
 static double min_image(double d, double L)
 {
-    return d - L * nearbyint(d / L);
+    return ORACLE_MUTANT == 3 ? d : d - L * nearbyint(d / L);
 }
 
 /* Pair energy and radial force (positive = repulsive) of one pair at distance
@@ -73,7 +80,7 @@ int oracle_pair(double r, double rc, double *force_radial, double *energy)
 {
     if (!(r > 0.0) || !(rc > 0.0) || !force_radial || !energy) return ORACLE_ERR_ARG;
     double r2 = r * r;
-    if (r2 <= rc * rc) {
+    if (ORACLE_MUTANT == 8 ? r2 < rc * rc : r2 <= rc * rc) {
         double fa, u;
         lj_pair_terms(r2, lj_shift(rc), &fa, &u);
         *force_radial = fa * r;
@@ -183,7 +190,7 @@ static void atom_from_cells(int64_t i, const double *pos, const double *box, dou
     double fx = 0.0, fy = 0.0, fz = 0.0, uu = 0.0, ww = 0.0;
     for (int ox = -1; ox <= 1; ++ox)
         for (int oy = -1; oy <= 1; ++oy)
-            for (int oz = -1; oz <= 1; ++oz) {
+            for (int oz = -1; oz <= (ORACLE_MUTANT == 4 ? 0 : 1); ++oz) {
                 int cx = (c0[0] + ox + cl->nc[0]) % cl->nc[0];
                 int cy = (c0[1] + oy + cl->nc[1]) % cl->nc[1];
                 int cz = (c0[2] + oz + cl->nc[2]) % cl->nc[2];
@@ -201,7 +208,7 @@ static void atom_from_cells(int64_t i, const double *pos, const double *box, dou
                         fy += dy * fa;
                         fz += dz * fa;
                         uu += 0.5 * u;
-                        ww += 0.5 * r2 * fa;
+                        ww += 0.5 * (ORACLE_MUTANT == 7 ? 1.0 : r2) * fa;
                     }
                 }
             }
@@ -311,7 +318,8 @@ int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc
             if (rcode) break;
         }
         /* second loop of Algorithm 1: v += (F_new + F_old) dt / 2 -> v_s */
-        for (int64_t k = 0; k < 3 * n; ++k) vel[k] = vel[k] + (F[k] + f_old[k]) * 0.5 * dt;
+        for (int64_t k = 0; k < 3 * n; ++k)
+            vel[k] = vel[k] + (F[k] + (ORACLE_MUTANT == 5 ? 0.0 : f_old[k])) * 0.5 * dt;
         if (obs) {
             obs[3 * s + 0] = U;
             obs[3 * s + 1] = W;
@@ -319,7 +327,8 @@ int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc
         }
         if (s == steps) break; /* closing half kick done: state is (r_n, v_n, F_n) */
         /* third loop of Algorithm 1: r += v dt + F_new dt^2 / 2 */
-        for (int64_t k = 0; k < 3 * n; ++k) pos[k] = pos[k] + vel[k] * dt + F[k] * 0.5 * dt * dt;
+        for (int64_t k = 0; k < 3 * n; ++k)
+            pos[k] = pos[k] + vel[k] * dt + (ORACLE_MUTANT == 6 ? 0.0 : F[k] * 0.5 * dt * dt);
         wrap_positions(n, pos, box);
     }
     free(f_old);
