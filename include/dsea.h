@@ -173,8 +173,9 @@ int dsea_batch_destroy(dsea_batch *batch);
 
 /* Time each candidate work-unit shape (tile_y x tile_z home cells) for
  * trial_steps steps on a scratch copy of the box and keep the fastest; the
- * choice is cached per (cells per axis, cell capacity, precision) and applied
- * to the box.  The tile shape never changes a result: each atom's force is
+ * choice is cached per size class (cells along y and z up to 16, cell layers
+ * per slice, cell capacity, precision), applied to the box and used as the
+ * default shape of later boxes of the same class.  The tile shape never changes a result: each atom's force is
  * summed in the same order whatever the shape.  *chosen (may be NULL)
  * receives the parameters in effect. */
 int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);

@@ -98,10 +98,9 @@ bool apply_tile(BoxDev &hb, double mean_cap, int ty, int tz)
     hb.units_per_slice = hb.tiles_y * hb.tiles_z;
     hb.staged_cells = (hb.cps + 2) * (ty + 2) * (tz + 2);
     if (hb.staged_cells > dsea::kMaxStagedCells) return false;
-    // room for the expected stage plus a quarter (plus the FP64 form's padding
-    // of each cell to 4 slots), never more than every slot; a multiple of 4
-    const double pad = hb.precision == DSEA_FP64 ? 3.0 * hb.staged_cells : 0.0;
-    const double expect = hb.staged_cells * mean_cap * 1.25 + 64.0 + pad;
+    // room for the expected stage plus a quarter, never more than every slot;
+    // a multiple of 4
+    const double expect = hb.staged_cells * mean_cap * 1.25 + 64.0;
     const double worst = (double)hb.staged_cells * hb.cap;
     hb.smem_atoms = ((int)std::ceil(std::min(expect, worst)) + 3) & ~3;
     return dsea::unit_smem_bytes(hb.precision, hb.staged_cells, hb.smem_atoms) <=
@@ -229,6 +228,14 @@ struct TuneKey {
                std::tie(o.nc0, o.nc1, o.nc2, o.cps, o.cap, o.precision);
     }
 };
+// Size class of the autotuner cache: the unit shape depends on the cells per
+// axis in the unit plane (up to 16, beyond which boxes behave alike), the
+// cell layers per slice, the cell capacity (a proxy for atoms per cell) and
+// the precision; the number of slices does not change the best shape.
+TuneKey size_class(const int *nc, int cps, int cap, int precision)
+{
+    return TuneKey{0, std::min(nc[1], 16), std::min(nc[2], 16), cps, cap, precision};
+}
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
@@ -277,6 +284,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
         cap = std::max(8, cap);
     }
     cap = (cap + 3) / 4 * 4;   // slot ranges start 16-byte aligned in every per-slot array
+    if (cap > 128) return DSEA_ERR_INVALID_ARG;   // a staging warp orders up to 128 arrivals
     hb.cap = cap;
     hb.n_slots = hb.n_cells * cap;
     if (hb.n_slots >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
@@ -295,7 +303,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     int ty = p.tile_y, tz = p.tile_z;
     if (ty == 0 || tz == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find({hb.nc[0], hb.nc[1], hb.nc[2], cps, cap, p.precision});
+        auto it = g_tune_cache.find(size_class(hb.nc, cps, cap, p.precision));
         if (it != g_tune_cache.end()) {
             ty = it->second.first;
             tz = it->second.second;
@@ -408,7 +416,9 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
         !b->d_launch_err)
         return DSEA_ERR_OOM;
     for (int q = 0; q < 2; ++q) {
-        hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * hb.n_cells);
+        // stayer and arrival counts of every cell, one allocation
+        hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * 2 * hb.n_cells);
+        hb.arr[q] = hb.cnt[q] ? hb.cnt[q] + hb.n_cells : nullptr;
         hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
         hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
         hb.v[q] = nullptr;
@@ -423,7 +433,7 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
         if (!hb.cnt[q] || !hb.id[q] || !hb.r[q] ||
             (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : !hb.v[q]))
             return DSEA_ERR_OOM;
-        CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * hb.n_cells, b->stream));
+        CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * 2 * hb.n_cells, b->stream));
     }
     CU(cudaMemsetAsync(hb.err, 0, sizeof(int), b->stream));
     // bin the initial atoms into the buffer of step 0
@@ -666,7 +676,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
     int rc = check_device_error(b);
     if (rc) return rc;
     BoxDev &hb = b->hb;
-    const TuneKey key{hb.nc[0], hb.nc[1], hb.nc[2], hb.cps, hb.cap, hb.precision};
+    const TuneKey key = size_class(hb.nc, hb.cps, hb.cap, hb.precision);
     std::pair<int, int> best{hb.tile_y, hb.tile_z};
     bool cached = false;
     {
@@ -682,7 +692,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         const int p = (int)(hb.step & 1);
         const int64_t step0 = hb.step;
         const int sync0 = hb.w_is_sync;
-        const size_t b_cnt = sizeof(unsigned long long) * hb.n_cells, b_id = sizeof(int) * hb.n_slots,
+        const size_t b_cnt = sizeof(unsigned long long) * 2 * hb.n_cells, b_id = sizeof(int) * hb.n_slots,
                      b_r = sizeof(double) * 3 * hb.n_slots, b_q = sizeof(float4) * hb.n_slots;
         const bool mixed = hb.precision == DSEA_MIXED;
         const size_t b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
@@ -916,7 +926,7 @@ int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, siz
     if (rc) return rc;
     const size_t per_slot = sizeof(int) + 3 * sizeof(double) +
                             (p.precision == DSEA_MIXED ? 3 * sizeof(float) + sizeof(float4) : 3 * sizeof(double));
-    size_t b = 2 * ((size_t)hb.n_cells * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
+    size_t b = 2 * ((size_t)hb.n_cells * 2 * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
     b += (size_t)hb.n_cells * 3 * sizeof(double);              // unit partials
     b += (size_t)desc->n_atoms * 9 * sizeof(double);           // read-back arrays
     b += 64 * 1024;                                            // descriptors, counters, plans

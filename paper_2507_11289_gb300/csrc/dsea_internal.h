@@ -23,7 +23,10 @@ enum : int {
 
 // One box as the kernels see it.  Slot layout: the state of a step lives in
 // one of two buffers (step parity).  Cell c owns slots [c*cap, c*cap + cap);
-// per-slot arrays are SoA (component k of slot t at k*n_slots + t).
+// per-slot arrays are SoA (component k of slot t at k*n_slots + t).  Within
+// a cell, the atoms that stayed in it during the last step fill the front
+// slots in the cell's canonical order and the atoms that arrived fill the
+// back slots (the last one first); readers order the arrivals by atom id.
 struct BoxDev {
     // geometry (Sec. 4: cells of edge >= rc, slices of cps cell layers in x)
     double L[3];
@@ -46,7 +49,8 @@ struct BoxDev {
     double rc2, ushift, dt;
     float rc2f, ushiftf;
     // state, two step-parity buffers
-    unsigned long long *cnt[2];  // per cell: (tag << 32) | count, tag = step + 1
+    unsigned long long *cnt[2];  // per cell: (tag << 32) | stayers, tag = step + 1
+    unsigned long long *arr[2];  // per cell: (tag << 32) | arrivals
     int *id[2];
     double *r[2];   // absolute positions, 3 * n_slots
     double *v[2];   // FP64 form: velocities (half-step after the first step), 3 * n_slots

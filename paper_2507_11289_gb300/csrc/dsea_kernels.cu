@@ -78,7 +78,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 // Shared-memory carve-up of one unit.
 struct Layout {
-    size_t cnt, start, gcell, atoms, id, slot, scr, ctab, red, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, id, slot, scr, ctab, red, ctr, total;
 };
 
 __host__ __device__ inline Layout make_layout(int precision, int staged_cells, int smem_atoms)
@@ -86,6 +86,7 @@ __host__ __device__ inline Layout make_layout(int precision, int staged_cells, i
     Layout L;
     size_t o = 0;
     L.cnt = o;   o += sizeof(int) * staged_cells;
+    L.nst = o;   o += sizeof(int) * staged_cells;   // stayers of each staged cell
     L.start = o; o += sizeof(int) * (staged_cells + 1);
     L.gcell = o; o += sizeof(int) * staged_cells;
     o = align16(o);
@@ -349,6 +350,29 @@ __device__ __forceinline__ int reserve_slot(unsigned long long *cnt, long long d
     return active ? base + rank : -1;
 }
 
+// Slot in the next-step buffer for each active lane's atom, whose new cell is
+// `dest`; `hcell` is the home cell the warp processes.  Atoms that stay take
+// the next front slots of their cell in the order the warp processes them
+// (the cell's canonical order), counted in n_stay (warp-uniform); atoms that
+// move reserve the next back slot of their new cell through its arrival
+// counter.  Returns -1 for inactive lanes and on overflow (error set).
+__device__ __forceinline__ long long place_slot(const BoxDev &B, int pn, long long hcell, long long dest,
+                                                bool own, unsigned tag, int lane, int &n_stay)
+{
+    const bool stay = own && dest == hcell;
+    const unsigned bs = __ballot_sync(kFull, stay);
+    const int k_stay = n_stay + __popc(bs & ((1u << lane) - 1u));
+    n_stay += __popc(bs);
+    const int k = reserve_slot(B.arr[pn], dest, own && !stay, tag, lane, B.err);
+    if (!own) return -1;
+    if (stay) return hcell * B.cap + k_stay;   // stayers never outnumber the cell's atoms
+    if (k >= B.cap) {
+        set_error(B.err, kErrCapacity);
+        return -1;
+    }
+    return dest * B.cap + (B.cap - 1 - k);
+}
+
 // Write one atom into slot `slot` of buffer `pn` (FP64 form).
 __device__ __forceinline__ void store_f64(const BoxDev &B, int pn, long long slot, int aid, double x,
                                           double y, double z, double vx, double vy, double vz)
@@ -431,6 +455,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     const unsigned tag = (unsigned)(s_abs + 1);
     const Layout Ly = make_layout(PREC, B.staged_cells, B.smem_atoms);
     int *s_cnt = reinterpret_cast<int *>(smem + Ly.cnt);
+    int *s_nst = reinterpret_cast<int *>(smem + Ly.nst);
     int *s_start = reinterpret_cast<int *>(smem + Ly.start);
     int *s_gcell = reinterpret_cast<int *>(smem + Ly.gcell);
     int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
@@ -458,24 +483,25 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         const int gy = wrap_index(y0 - 1 + ly, B.nc[1]);
         const int gz = wrap_index(z0 - 1 + lz, B.nc[2]);
         const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
-        const unsigned long long w = __ldcg(B.cnt[p] + gc);
-        int c = ((unsigned)(w >> 32) == tag) ? (int)(unsigned)w : 0;
-        if (c > B.cap) {
+        const unsigned long long ws = __ldcg(B.cnt[p] + gc), wa = __ldcg(B.arr[p] + gc);
+        int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;   // stayers (front)
+        int n_a = ((unsigned)(wa >> 32) == tag) ? (int)(unsigned)wa : 0;   // arrivals (back)
+        if (n_s + n_a > B.cap) {   // the two ends met: the cell overflowed
             set_error(B.err, kErrCapacity);
-            c = B.cap;
+            n_s = min(n_s, B.cap);
+            n_a = B.cap - n_s;
         }
-        s_cnt[k] = c;
+        s_cnt[k] = n_s + n_a;
+        s_nst[k] = n_s;
         s_gcell[k] = gc;
     }
     __syncthreads();
-    // 2. exclusive scan (warp 0, contiguous chunks per lane).  FP64 cells
-    // start on a multiple of 4 atoms so that their 8- and 4-byte arrays can
-    // be staged in 16-byte copies.
+    // 2. exclusive scan (warp 0, contiguous chunks per lane)
     if (warp == 0) {
         const int per = (n_staged + 31) / 32;
         const int b = lane * per, e = min(b + per, n_staged);
         int sum = 0;
-        for (int k = b; k < e; ++k) sum += PREC == 0 ? (s_cnt[k] + 3) & ~3 : s_cnt[k];
+        for (int k = b; k < e; ++k) sum += s_cnt[k];
         int incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(kFull, incl, o);
@@ -484,7 +510,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         int run = incl - sum;
         for (int k = b; k < e; ++k) {
             s_start[k] = run;
-            run += PREC == 0 ? (s_cnt[k] + 3) & ~3 : s_cnt[k];
+            run += s_cnt[k];
         }
         if (lane == 31) s_start[n_staged] = incl;
     }
@@ -493,138 +519,34 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         if (tid == 0) set_error(B.err, kErrCapacity);
         return;
     }
-    // 3. stage atoms, each cell sorted by atom id.  3a: every warp issues
-    // asynchronous 16-byte copies of its cells' slots in slot order and moves
-    // on without waiting; 3b: after one wait and barrier, each cell is sorted
-    // in place by atom id (warp per cell, lanes rank their atoms by shuffles).
+    // 3. stage atoms in each cell's canonical order: the stayers (front
+    // slots) as they are, then the arrivals (back slots) ordered by atom id.
+    // Mixed form: every warp issues asynchronous 16-byte copies of its cells'
+    // two slot ranges and moves on; after one wait and barrier, each cell's
+    // arrivals are ordered in place.  FP64 form: lanes load their atoms (L2)
+    // and write them to their place.
     const long long S = B.n_slots;
-    if (B.cap <= 128) {
+    if (PREC == 1) {
         for (int k = warp; k < n_staged; k += kWarps) {
             const int c = s_cnt[k];
             if (c == 0) continue;
+            const int n_s = s_nst[k], n_a = c - n_s;
             const long long base = (long long)s_gcell[k] * B.cap;
             const int st = s_start[k];
-            if (PREC == 1) {
-                for (int a = lane; a < c; a += 32) cp_async16(s_q + st + a, B.q[p] + base + a);
-            } else {
-                const int n2 = (c + 1) >> 1, n4 = (c + 3) >> 2;   // 16-byte chunks
-                for (int q = lane; q < 3 * n2 + n4; q += 32) {
-                    if (q < 3 * n2) {
-                        const int d = q / n2, ch = q - d * n2;
-                        double *dst = (d == 0 ? s_x : (d == 1 ? s_y : s_z)) + st + 2 * ch;
-                        cp_async16(dst, B.r[p] + d * S + base + 2 * ch);
-                    } else {
-                        const int ch = q - 3 * n2;
-                        cp_async16(s_id + st + 4 * ch, B.id[p] + base + 4 * ch);
-                    }
-                }
+            for (int a = lane; a < c; a += 32) {
+                const long long src = a < n_s ? base + a : base + B.cap - n_a + (a - n_s);
+                cp_async16(s_q + st + a, B.q[p] + src);
             }
         }
         cp_async_wait_all();
         __syncthreads();
-        for (int k = warp; k < n_staged; k += kWarps) {
-            const int c = s_cnt[k];
-            if (c == 0) continue;
-            const long long base = (long long)s_gcell[k] * B.cap;
-            const int st = s_start[k];
-            const int nm = (c + 31) >> 5;   // atoms per lane (<= 4)
-            double shx = 0.0, shy = 0.0, shz = 0.0;
-            if (PREC == 0) {   // periodic image shift of this staged cell
-                const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
-                const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
-                shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
-                shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
-                shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
-            }
-            if (nm == 1) {   // the common case: one atom per lane
-                int id0 = 0x7fffffff;
-                float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f);
-                double x0v = 0.0, y0v = 0.0, z0v = 0.0;
-                if (lane < c) {
-                    if (PREC == 1) {
-                        q0 = s_q[st + lane];
-                        id0 = __float_as_int(q0.w);
-                    } else {
-                        x0v = s_x[st + lane] + shx;
-                        y0v = s_y[st + lane] + shy;
-                        z0v = s_z[st + lane] + shz;
-                        id0 = s_id[st + lane];
-                    }
-                }
-                int rank = 0;
-                for (int t = 0; t < c; ++t) rank += (__shfl_sync(kFull, id0, t) < id0) ? 1 : 0;
-                __syncwarp();   // every lane has read the cell before any writes
-                if (lane < c) {
-                    const int dst = st + rank;
-                    s_slot[dst] = (int)(base + lane);
-                    if (PREC == 1) {
-                        s_q[dst] = q0;
-                    } else {
-                        s_x[dst] = x0v;
-                        s_y[dst] = y0v;
-                        s_z[dst] = z0v;
-                        s_id[dst] = id0;
-                    }
-                }
-                continue;
-            }
-            int idm[4];
-            float4 qm[4];
-            double xm[4], ym[4], zm[4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int a = lane + 32 * m;
-                idm[m] = 0x7fffffff;
-                if (m < nm && a < c) {
-                    if (PREC == 1) {
-                        qm[m] = s_q[st + a];
-                        idm[m] = __float_as_int(qm[m].w);
-                    } else {
-                        xm[m] = s_x[st + a] + shx;
-                        ym[m] = s_y[st + a] + shy;
-                        zm[m] = s_z[st + a] + shz;
-                        idm[m] = s_id[st + a];
-                    }
-                }
-            }
-            int rk[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int mb = 0; mb < 4; ++mb) {
-                if (mb < nm) {
-                    const int lim = min(32, c - 32 * mb);
-                    for (int t = 0; t < lim; ++t) {
-                        const int o = __shfl_sync(kFull, idm[mb], t);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            if (m < nm) rk[m] += (o < idm[m]) ? 1 : 0;
-                    }
-                }
-            }
-            __syncwarp();   // every lane has read the cell before any writes
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int a = lane + 32 * m;
-                if (m < nm && a < c) {
-                    const int dst = st + rk[m];
-                    s_slot[dst] = (int)(base + a);
-                    if (PREC == 1) {
-                        s_q[dst] = qm[m];
-                    } else {
-                        s_x[dst] = xm[m];
-                        s_y[dst] = ym[m];
-                        s_z[dst] = zm[m];
-                        s_id[dst] = idm[m];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    } else {
+    }
     for (int k = warp; k < n_staged; k += kWarps) {
         const int c = s_cnt[k];
         if (c == 0) continue;
+        const int n_s = s_nst[k], n_a = c - n_s;
         const long long base = (long long)s_gcell[k] * B.cap;
-        const int *ids = B.id[p] + base;
+        const int st = s_start[k];
         double shx = 0.0, shy = 0.0, shz = 0.0;
         if (PREC == 0) {   // periodic image shift of this staged cell
             const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
@@ -633,32 +555,81 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
             shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
             shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
         }
-        for (int a0 = 0; a0 < c; a0 += 32) {
-            const int a = a0 + lane;
-            const int myid = a < c ? __ldcg(ids + a) : 0x7fffffff;
-            int rank = 0;
-            for (int b0 = 0; b0 < c; b0 += 32) {
-                const int other = (b0 + lane < c) ? __ldcg(ids + b0 + lane) : 0x7fffffff;
-                const int lim = min(32, c - b0);
-                for (int t = 0; t < lim; ++t) rank += (__shfl_sync(kFull, other, t) < myid) ? 1 : 0;
+        for (int a = lane; a < n_s; a += 32) {
+            const long long slot = base + a;
+            s_slot[st + a] = (int)slot;
+            if (PREC == 0) {
+                s_x[st + a] = __ldcg(B.r[p] + slot) + shx;
+                s_y[st + a] = __ldcg(B.r[p] + S + slot) + shy;
+                s_z[st + a] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+                s_id[st + a] = __ldcg(B.id[p] + slot);
             }
-            if (a < c) {
-                const int dst = s_start[k] + rank;
-                const long long slot = base + a;
-                s_slot[dst] = (int)slot;
+        }
+        if (n_a == 0) continue;
+        // arrivals: rank by atom id among themselves (up to 4 per lane)
+        const int fa = st + n_s;                      // staged position of the first arrival
+        const long long abase = base + B.cap - n_a;   // slot of the first arrival
+        if (n_a > 128) {
+            if (lane == 0) set_error(B.err, kErrCapacity);
+            continue;
+        }
+        const int nm = (n_a + 31) >> 5;
+        int idm[4];
+        float4 qm[4];
+        double xm[4], ym[4], zm[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int a = lane + 32 * m;
+            idm[m] = 0x7fffffff;
+            if (m < nm && a < n_a) {
                 if (PREC == 1) {
-                    s_q[dst] = __ldcg(B.q[p] + slot);
+                    qm[m] = s_q[fa + a];
+                    idm[m] = __float_as_int(qm[m].w);
                 } else {
-                    s_x[dst] = __ldcg(B.r[p] + slot) + shx;
-                    s_y[dst] = __ldcg(B.r[p] + S + slot) + shy;
-                    s_z[dst] = __ldcg(B.r[p] + 2 * S + slot) + shz;
-                    s_id[dst] = myid;
+                    const long long slot = abase + a;
+                    xm[m] = __ldcg(B.r[p] + slot) + shx;
+                    ym[m] = __ldcg(B.r[p] + S + slot) + shy;
+                    zm[m] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+                    idm[m] = __ldcg(B.id[p] + slot);
+                }
+            }
+        }
+        int rk[4] = {0, 0, 0, 0};
+        if (nm == 1) {
+            for (int t = 0; t < n_a; ++t) rk[0] += (__shfl_sync(kFull, idm[0], t) < idm[0]) ? 1 : 0;
+        } else {
+#pragma unroll
+            for (int mb = 0; mb < 4; ++mb) {
+                if (mb < nm) {
+                    const int lim = min(32, n_a - 32 * mb);
+                    for (int t = 0; t < lim; ++t) {
+                        const int o = __shfl_sync(kFull, idm[mb], t);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (m < nm) rk[m] += (o < idm[m]) ? 1 : 0;
+                    }
+                }
+            }
+        }
+        __syncwarp();   // every lane has read the arrivals before any writes
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int a = lane + 32 * m;
+            if (m < nm && a < n_a) {
+                const int dst = fa + rk[m];
+                s_slot[dst] = (int)(abase + a);
+                if (PREC == 1) {
+                    s_q[dst] = qm[m];
+                } else {
+                    s_x[dst] = xm[m];
+                    s_y[dst] = ym[m];
+                    s_z[dst] = zm[m];
+                    s_id[dst] = idm[m];
                 }
             }
         }
     }
     __syncthreads();
-    }   // cells of more than 128 slots: the loads above wait per cell
 
     // 4./5. forces, then kick, drift and rebin, warp per home cell.  Without
     // a reduction the home cells are handed out dynamically; with one, in a
@@ -681,6 +652,8 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         const int n_i = s_cnt[kh];
         const int hs = s_start[kh];
         const int cg[3] = {x0 + hx, y0 + hy, z0 + hz};   // home cell (within the box)
+        const long long hcell = s_gcell[kh];
+        int n_stay = 0;   // atoms of this cell that stay in it, written to its front slots in order
         double *ctab = reinterpret_cast<double *>(smem + Ly.ctab) + warp * 9;
         if (PREC == 1) {
             if (lane < 9) {
@@ -706,9 +679,10 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                 double *pr = reinterpret_cast<double *>(pref);          // [3][32]
                 float *pv = reinterpret_cast<float *>(pref + 32 * 3 * 8);  // [3][32]
                 const long long hbase = (long long)s_gcell[kh] * B.cap;
-                const bool pf = n_i <= 32;
+                const int n_front = s_nst[kh];   // stayers: slots [0, n_front); arrivals at the back
+                const bool pf = n_front <= 32;
                 if (pf) {
-                    const int n2 = (n_i + 1) >> 1, n4 = (n_i + 3) >> 2;
+                    const int n2 = (n_front + 1) >> 1, n4 = (n_front + 3) >> 2;
                     for (int q = lane; q < 3 * (n2 + n4); q += 32) {
                         if (q < 3 * n2) {
                             const int d = q / n2, ch = q - d * n2;
@@ -733,8 +707,9 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                     aid = __float_as_int(qo.w);
                     for (int d = 0; d < 3; ++d) {
                         const int a = (int)(slot - hbase);
-                        rr[d] = pf ? pr[32 * d + a] : __ldcg(B.r[p] + d * S + slot);
-                        vv[d] = pf ? pv[32 * d + a] : __ldcg(B.vf[p] + d * S + slot);
+                        const bool hit = pf && a < n_front;
+                        rr[d] = hit ? pr[32 * d + a] : __ldcg(B.r[p] + d * S + slot);
+                        vv[d] = hit ? pv[32 * d + a] : __ldcg(B.vf[p] + d * S + slot);
                     }
                     if (OBS) {
                         // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
@@ -770,12 +745,10 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                         if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
                         dest = ((long long)c3[0] * B.nc[1] + c3[1]) * B.nc[2] + c3[2];
                     }
-                    const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
-                    if (own) {
-                        if (k >= B.cap) set_error(B.err, kErrCapacity);
-                        else store_mixed(B, pn, dest * B.cap + k, aid, rr[0], rr[1], rr[2], vv[0], vv[1],
-                                         vv[2], qn[0], qn[1], qn[2]);
-                    }
+                    const long long slot_n = place_slot(B, pn, hcell, dest, own, tag_next, lane, n_stay);
+                    if (slot_n >= 0)
+                        store_mixed(B, pn, slot_n, aid, rr[0], rr[1], rr[2], vv[0], vv[1], vv[2], qn[0], qn[1],
+                                    qn[2]);
                 }
             } else {
                 Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -847,15 +820,15 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                         if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
                         dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
                     }
-                    const int k = reserve_slot(B.cnt[pn], dest, own, tag_next, lane, B.err);
-                    if (own) {
-                        if (k >= B.cap) set_error(B.err, kErrCapacity);
-                        else store_f64(B, pn, dest * B.cap + k, aid, rx, ry, rz, vx, vy, vz);
-                    }
+                    const long long slot_n = place_slot(B, pn, hcell, dest, own, tag_next, lane, n_stay);
+                    if (slot_n >= 0) store_f64(B, pn, slot_n, aid, rx, ry, rz, vx, vy, vz);
                 }
             }
             __syncwarp();
         }
+        // every home cell publishes how many atoms stayed in it, empty or not
+        if (INTEGRATE && lane == 0)
+            B.cnt[pn][hcell] = ((unsigned long long)tag_next << 32) | (unsigned long long)n_stay;
         if (OBS) {
             h += kWarps;
         } else {
@@ -924,8 +897,10 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
             cz = cell_of(z, B.inv_lc[2], B.nc[2]);
             dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
         }
-        const int k = reserve_slot(B.cnt[p], dest, own, tag, lane, B.err);
+        // every initial atom is an arrival (back slots); readers order them by id
+        const int k = reserve_slot(B.arr[p], dest, own, tag, lane, B.err);
         if (own) {
+            const long long slot = dest * B.cap + (B.cap - 1 - k);
             if (k >= B.cap) {
                 set_error(B.err, kErrCapacity);
             } else if (PREC == 1) {
@@ -933,10 +908,9 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
                 const float qx = (float)(x - ((double)cx + 0.5) * B.lc[0]);
                 const float qy = (float)(y - ((double)cy + 0.5) * B.lc[1]);
                 const float qz = (float)(z - ((double)cz + 0.5) * B.lc[2]);
-                store_mixed(B, p, dest * B.cap + k, (int)i, x, y, z, (float)vx, (float)vy, (float)vz, qx,
-                            qy, qz);
+                store_mixed(B, p, slot, (int)i, x, y, z, (float)vx, (float)vy, (float)vz, qx, qy, qz);
             } else {
-                store_f64(B, p, dest * B.cap + k, (int)i, x, y, z, vx, vy, vz);
+                store_f64(B, p, slot, (int)i, x, y, z, vx, vy, vz);
             }
         }
     }

@@ -80,7 +80,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     };
     const size_t o_desc = take(sizeof(dsea::BoxDev));
     const size_t o_err = take(sizeof(int));
-    const size_t o_cnt = take(sizeof(unsigned long long) * hb.n_cells);
+    const size_t o_cnt = take(sizeof(unsigned long long) * 2 * hb.n_cells);   // stayers, arrivals
     const size_t o_id = take(sizeof(int) * hb.n_slots);
     const size_t o_r = take(sizeof(double) * 3 * hb.n_slots);
     const size_t o_v = take((precision == DSEA_MIXED ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots);
@@ -97,6 +97,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     hb.err = reinterpret_cast<int *>(base + o_err);
     for (int q = 0; q < 2; ++q) {   // one configuration: step 0 uses buffer 0 only
         hb.cnt[q] = reinterpret_cast<unsigned long long *>(base + o_cnt);
+        hb.arr[q] = hb.cnt[q] + hb.n_cells;
         hb.id[q] = reinterpret_cast<int *>(base + o_id);
         hb.r[q] = reinterpret_cast<double *>(base + o_r);
         hb.v[q] = precision == DSEA_MIXED ? nullptr : reinterpret_cast<double *>(base + o_v);
@@ -113,7 +114,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     hb.withhold_slice = -1;
     hb.wait_limit_ns = 5000000000LL;
     // the scratch keeps the previous call's contents: clear what must start at zero
-    cudaError_t e = cudaMemsetAsync(hb.cnt[0], 0, sizeof(unsigned long long) * hb.n_cells, st);
+    cudaError_t e = cudaMemsetAsync(hb.cnt[0], 0, sizeof(unsigned long long) * 2 * hb.n_cells, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(hb.err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db, &hb, sizeof(hb), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = dsea::launch_bin(hb, db, pos_dev, vel_dev, st);
