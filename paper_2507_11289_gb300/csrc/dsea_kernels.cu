@@ -76,9 +76,22 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// floor(a / d) for 0 <= a < 2^22 through the FP32 reciprocal inv_d = 1/d
+// (a few instructions instead of an integer division).  Exact: (a + 1/2)/d
+// lies at least 1/(2d) away from an integer, far above the rounding error.
+__device__ __forceinline__ int qdiv(int a, float inv_d)
+{
+    return (int)(((float)a + 0.5f) * inv_d);
+}
+
+__device__ __forceinline__ float inv_of(int d)
+{
+    return __frcp_rn((float)d);
+}
+
 // Shared-memory carve-up of one unit.
 struct Layout {
-    size_t cnt, nst, start, gcell, atoms, id, slot, scr, ctab, red, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, id, slot, scr, ctab, tab, red, ctr, total;
 };
 
 __host__ __device__ inline Layout make_layout(int precision, int staged_cells, int smem_atoms)
@@ -104,6 +117,7 @@ __host__ __device__ inline Layout make_layout(int precision, int staged_cells, i
     L.scr = o;                                  // FP64: partial sums; mixed: r/v prefetch
     o += precision == 1 ? (size_t)kWarps * kPrefBytes : sizeof(double) * kThreads * 5;
     L.ctab = o; o += sizeof(double) * kWarps * 9;   // mixed: neighbour cell centres
+    L.tab = o;  o += sizeof(int2) * kWarps * 32;     // mixed: neighbour cell table per warp
     L.red = o;  o += sizeof(double) * kWarps * 3;
     L.ctr = o;  o += 16;
     L.total = align16(o);
@@ -224,47 +238,80 @@ __device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const fl
 // returns the totals of atom base + l.
 template <bool OBS>
 __device__ __forceinline__ void packed_forces(const BoxDev &B, const float4 *s_q, const int *s_start,
-                                              const int *s_cnt, int hx, int hy, int hz, int EY, int EZ,
-                                              int base, int nin, int lane, float &fx, float &fy,
+                                              const int *s_cnt, int2 *tab, int hx, int hy, int hz, int EY,
+                                              int EZ, int base, int nin, int lane, float &fx, float &fy,
                                               float &fz, float &uu, float &ww)
 {
     const int np = (nin + 1) >> 1;
-    const int ns = 32 / np;
-    const int pi = lane % np, g = lane / np;
+    const float inv_np = inv_of(np);
+    const int ns = qdiv(32, inv_np);
+    const int g = qdiv(lane, inv_np), pi = lane - g * np;
     const bool act = g < ns;
     const int a0 = 2 * pi, a1 = min(2 * pi + 1, nin - 1);   // odd nin: the last pair repeats an atom
     Acc2 acc = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)};
+    // table of the 26 neighbour cells: staged start and prefix of the counts
+    // (lane 26 holds the total), so the cells read as one list
+    {
+        int cs = 0, cn = 0;
+        if (lane < 26) {
+            const int kk = lane + (lane >= 13 ? 1 : 0);
+            const int ox = kk / 9 - 1, oy = (kk / 3) % 3 - 1, oz = kk % 3 - 1;
+            const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+            cs = s_start[kn];
+            cn = s_cnt[kn];
+        }
+        int incl = cn;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane <= 26) tab[lane] = make_int2(cs, incl - cn);
+        __syncwarp();
+    }
     if (act) {
         const float4 q0 = s_q[base + a0], q1 = s_q[base + a1];
         const float2 X = make_float2(q0.x, q1.x), Y = make_float2(q0.y, q1.y), Z = make_float2(q0.z, q1.z);
         const unsigned rcb = __float_as_uint(B.rc2f);
         const float rc2f = B.rc2f, ush = B.ushiftf;
-        DSEA_CELL_UNROLL
-        for (int ox = -1; ox <= 1; ++ox)
-            DSEA_CELL_UNROLL
-            for (int oy = -1; oy <= 1; ++oy)
-                DSEA_CELL_UNROLL
-                for (int oz = -1; oz <= 1; ++oz) {
-                    const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
-                    const int cs = s_start[kn], cn = s_cnt[kn];
-                    // home atoms in the neighbour cell's centred frame
-                    const float2 XS = f2sub(X, f2splat((float)ox * B.lcf[0]));
-                    const float2 YS = f2sub(Y, f2splat((float)oy * B.lcf[1]));
-                    const float2 ZS = f2sub(Z, f2splat((float)oz * B.lcf[2]));
-                    const float4 *qc = s_q + cs;
-                    int t = g;
-                    if (!OBS && (ox | oy | oz) != 0) {
-                        // no self pair here: two independent candidates per iteration
-                        for (; t + ns < cn; t += 2 * ns) {
-                            const float4 pj0 = qc[t], pj1 = qc[t + ns];
-                            pair2<false, false>(XS, YS, ZS, pj0, rc2f, rcb, ush, acc);
-                            pair2<false, false>(XS, YS, ZS, pj1, rc2f, rcb, ush, acc);
-                        }
-                        if (t < cn) pair2<false, false>(XS, YS, ZS, qc[t], rc2f, rcb, ush, acc);
-                    } else {
-                        for (; t < cn; t += ns) pair2<true, OBS>(XS, YS, ZS, qc[t], rc2f, rcb, ush, acc);
-                    }
+        // the home cell (it holds the atoms themselves: exact test), split by stride
+        {
+            const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
+            const float4 *qc = s_q + s_start[kh];
+            const int cn = s_cnt[kh];
+            for (int t = g; t < cn; t += ns) pair2<true, OBS>(X, Y, Z, qc[t], rc2f, rcb, ush, acc);
+        }
+        // the 26 neighbour cells as one list, an equal contiguous share per split
+        const int M = tab[26].y;
+        const int chunk = qdiv(M + ns - 1, inv_of(ns));
+        int t = g * chunk;
+        const int e = min(M, t + chunk);
+        if (t < e) {
+            int lo = 0, hi = 25;   // the cell holding list position t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tab[mid].y <= t) lo = mid; else hi = mid - 1;
+            }
+            int k = lo;
+            int end = tab[k + 1].y, off = tab[k].x - tab[k].y;
+            float2 XS, YS, ZS;
+            auto frame = [&](int kc) {   // home atoms in neighbour cell kc's centred frame
+                const int kk = kc + (kc >= 13 ? 1 : 0);
+                XS = f2sub(X, f2splat((float)(kk / 9 - 1) * B.lcf[0]));
+                YS = f2sub(Y, f2splat((float)((kk / 3) % 3 - 1) * B.lcf[1]));
+                ZS = f2sub(Z, f2splat((float)(kk % 3 - 1) * B.lcf[2]));
+            };
+            frame(k);
+            for (; t < e; ++t) {
+                while (t == end) {   // next non-empty cell
+                    ++k;
+                    end = tab[k + 1].y;
+                    off = tab[k].x - tab[k].y;
+                    frame(k);
                 }
+                if (OBS) pair2<true, true>(XS, YS, ZS, s_q[off + t], rc2f, rcb, ush, acc);
+                else pair2<false, false>(XS, YS, ZS, s_q[off + t], rc2f, rcb, ush, acc);
+            }
+        }
     }
     const float2 FX = acc.fx, FY = acc.fy, FZ = acc.fz, UU = acc.u, WW = acc.w;
     // combine the ns partials of each atom pair into lane pi, in split order
@@ -468,17 +515,19 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     int *s_id = reinterpret_cast<int *>(smem + Ly.id);
 
     // unit geometry
-    const int tyi = tile / B.tiles_z, tzi = tile - (tile / B.tiles_z) * B.tiles_z;
+    const int tyi = qdiv(tile, inv_of(B.tiles_z)), tzi = tile - tyi * B.tiles_z;
     const int y0 = tyi * B.tile_y, z0 = tzi * B.tile_z;
     const int ny = min(B.tile_y, B.nc[1] - y0), nz = min(B.tile_z, B.nc[2] - z0);
     const int x0 = j * B.cps, nx = B.cps;
     const int EY = ny + 2, EZ = nz + 2;
     const int n_staged = (nx + 2) * EY * EZ;
+    const float inv_eyez = inv_of(EY * EZ), inv_ez = inv_of(EZ), inv_nynz = inv_of(ny * nz),
+                inv_nz = inv_of(nz), inv_cps = inv_of(B.cps);
 
     // 1. counts of the staged cells
     if (tid == 0) *s_ctr = 0;
     for (int k = tid; k < n_staged; k += kThreads) {
-        const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
+        const int lx = qdiv(k, inv_eyez), rem = k - lx * EY * EZ, ly = qdiv(rem, inv_ez), lz = rem - ly * EZ;
         const int gx = wrap_index(x0 - 1 + lx, B.nc[0]);
         const int gy = wrap_index(y0 - 1 + ly, B.nc[1]);
         const int gz = wrap_index(z0 - 1 + lz, B.nc[2]);
@@ -549,7 +598,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         const int st = s_start[k];
         double shx = 0.0, shy = 0.0, shz = 0.0;
         if (PREC == 0) {   // periodic image shift of this staged cell
-            const int lx = k / (EY * EZ), rem = k - lx * EY * EZ, ly = rem / EZ, lz = rem - ly * EZ;
+            const int lx = qdiv(k, inv_eyez), rem = k - lx * EY * EZ, ly = qdiv(rem, inv_ez), lz = rem - ly * EZ;
             const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
             shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
             shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
@@ -647,7 +696,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         h = __shfl_sync(kFull, h, 0);
     }
     while (h < n_home) {
-        const int hx = h / (ny * nz), hr = h - hx * ny * nz, hy = hr / nz, hz = hr - hy * nz;
+        const int hx = qdiv(h, inv_nynz), hr = h - hx * ny * nz, hy = qdiv(hr, inv_nz), hz = hr - hy * nz;
         const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
         const int n_i = s_cnt[kh];
         const int hs = s_start[kh];
@@ -664,8 +713,9 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         }
         for (int ib = 0; ib < n_i; ib += 32) {
             const int nin = min(32, n_i - ib);
-            const int ns = 32 / nin;
-            const int li = lane % nin, g = lane / nin;
+            const float inv_nin = inv_of(nin);
+            const int ns = qdiv(32, inv_nin);
+            const int g = qdiv(lane, inv_nin), li = lane - g * nin;
             const bool act = g < ns;
             const int is = hs + ib + li;
             const bool own = lane < nin;
@@ -683,18 +733,14 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                 const bool pf = n_front <= 32;
                 if (pf) {
                     const int n2 = (n_front + 1) >> 1, n4 = (n_front + 3) >> 2;
-                    for (int q = lane; q < 3 * (n2 + n4); q += 32) {
-                        if (q < 3 * n2) {
-                            const int d = q / n2, ch = q - d * n2;
-                            cp_async16(pr + 32 * d + 2 * ch, B.r[p] + d * S + hbase + 2 * ch);
-                        } else {
-                            const int q2 = q - 3 * n2, d = q2 / n4, ch = q2 - d * n4;
-                            cp_async16(pv + 32 * d + 4 * ch, B.vf[p] + d * S + hbase + 4 * ch);
-                        }
+                    for (int d = 0; d < 3; ++d) {
+                        if (lane < n2) cp_async16(pr + 32 * d + 2 * lane, B.r[p] + d * S + hbase + 2 * lane);
+                        if (lane < n4) cp_async16(pv + 32 * d + 4 * lane, B.vf[p] + d * S + hbase + 4 * lane);
                     }
                 }
                 float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
-                packed_forces<OBS>(B, s_q, s_start, s_cnt, hx, hy, hz, EY, EZ, hs + ib, nin, lane, fx,
+                packed_forces<OBS>(B, s_q, s_start, s_cnt, reinterpret_cast<int2 *>(smem + Ly.tab) + warp * 32,
+                                   hx, hy, hz, EY, EZ, hs + ib, nin, lane, fx,
                                    fy, fz, uu, ww);
                 cp_async_wait_all();
                 __syncwarp();
@@ -740,7 +786,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                         for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
                             c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], ctab + 3 * d, B.lc[d],
                                               1.0f / B.lcf[d], B.L[d], B.nc[d], qn[d]);
-                        const int dj = c3[0] / B.cps - j;
+                        const int dj = qdiv(c3[0], inv_cps) - j;
                         const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
                         if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
                         dest = ((long long)c3[0] * B.nc[1] + c3[1]) * B.nc[2] + c3[2];
@@ -815,7 +861,7 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
                         const int cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
                         const int cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
                         const int cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
-                        const int dj = cx / B.cps - j;
+                        const int dj = qdiv(cx, inv_cps) - j;
                         const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
                         if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
                         dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
@@ -972,68 +1018,67 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring(RingPla
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;
-    __shared__ long long s_ticket;
+    __shared__ int s_dec[3];
     __shared__ int s_box;
     __shared__ int s_go;
     const int tid = threadIdx.x;
     if (tid == 0) s_box = -1;
     __syncthreads();
     while (true) {
-        if (tid == 0) s_ticket = (long long)atomicAdd(plan.ticket, 1ULL);
-        __syncthreads();
-        const long long t = s_ticket;
-        if (t >= plan.total) break;
-        // decode: relative step, box, unit within the box's step
-        int lo = 0, hi = plan.n_steps - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (plan.step_base[mid] <= t) lo = mid; else hi = mid - 1;
-        }
-        const int s_rel = lo;
-        const long long r = t - plan.step_base[s_rel];
-        int bl = 0, bh = plan.active[s_rel] - 1;
-        while (bl < bh) {
-            const int mid = (bl + bh + 1) >> 1;
-            if (plan.cum_units[mid] <= r) bl = mid; else bh = mid - 1;
-        }
-        const int b = bl;
-        const long long m = r - plan.cum_units[b];
-        if (b != s_box) {
-            __syncthreads();
-            if (tid == 0) {
-                sB = plan.boxes[b];
-                s_box = b;
-            }
-            __syncthreads();
-        }
-        const long long s_abs = sB.step + s_rel;
-        const int ups = sB.units_per_slice;
-        const int jj = (int)(m / ups), tile = (int)(m - (long long)jj * ups);
-        const int j = ring_slice(jj, s_abs, sB.n_slices);
-        // bounded wait for slices j-2..j+2 at the previous level.  A box that
-        // has already failed (capacity, migration) drains its remaining units
-        // without work so that nothing waits on it; a wait that expires stops
-        // the whole launch and marks every box of it.
+        // thread 0 takes the next ticket, decodes it into (relative step, box,
+        // slice, tile), loads the box's descriptor if it changed, and waits
+        // (bounded) until slices j-2..j+2 of the previous level are complete.
+        // A box that has already failed (capacity, migration) drains its
+        // remaining units without work so that nothing waits on it; a wait that
+        // expires stops the whole launch and marks every box of it.
         if (tid == 0) {
             int go = 1;   // 0: stop the CTA, 1: run the unit, 2: skip it
-            if (ld_volatile_int(plan.err) != 0) go = 0;
-            else if (ld_volatile_int(sB.err) != 0) go = 2;
-            if (go == 1 && s_rel > 0) {
-                const unsigned need = (unsigned)ups * (unsigned)s_rel;
-                const unsigned long long t0 = global_ns();
-                for (int d = -2; d <= 2 && go == 1; ++d) {
-                    const int k = wrap_index(j + d, sB.n_slices);
-                    unsigned sleep = 32;
-                    while (ld_acquire(sB.done + k) < need) {
-                        if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
-                        if ((long long)(global_ns() - t0) > sB.wait_limit_ns) {
-                            atomicCAS(plan.err, 0, kErrTimeout);
-                            for (int q = 0; q < plan.n_boxes; ++q) set_error(plan.boxes[q].err, kErrTimeout);
-                            go = 0;
-                            break;
+            const long long t = (long long)atomicAdd(plan.ticket, 1ULL);
+            if (t >= plan.total) {
+                go = 0;
+            } else {
+                int lo = 0, hi = plan.n_steps - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (plan.step_base[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                const int s_rel = lo;
+                const long long r = t - plan.step_base[s_rel];
+                int bl = 0, bh = plan.active[s_rel] - 1;
+                while (bl < bh) {
+                    const int mid = (bl + bh + 1) >> 1;
+                    if (plan.cum_units[mid] <= r) bl = mid; else bh = mid - 1;
+                }
+                if (bl != s_box) {   // no other thread reads sB between the unit barriers
+                    sB = plan.boxes[bl];
+                    s_box = bl;
+                }
+                const int m = (int)(r - plan.cum_units[bl]);
+                const int ups = sB.units_per_slice;
+                const int jj = m / ups;
+                const int j = ring_slice(jj, sB.step + s_rel, sB.n_slices);
+                s_dec[0] = s_rel;
+                s_dec[1] = j;
+                s_dec[2] = m - jj * ups;
+                if (ld_volatile_int(plan.err) != 0) go = 0;
+                else if (ld_volatile_int(sB.err) != 0) go = 2;
+                if (go == 1 && s_rel > 0) {
+                    const unsigned need = (unsigned)ups * (unsigned)s_rel;
+                    const unsigned long long t0 = global_ns();
+                    for (int d = -2; d <= 2 && go == 1; ++d) {
+                        const int k = wrap_index(j + d, sB.n_slices);
+                        unsigned sleep = 32;
+                        while (ld_acquire(sB.done + k) < need) {
+                            if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
+                            if ((long long)(global_ns() - t0) > sB.wait_limit_ns) {
+                                atomicCAS(plan.err, 0, kErrTimeout);
+                                for (int q = 0; q < plan.n_boxes; ++q) set_error(plan.boxes[q].err, kErrTimeout);
+                                go = 0;
+                                break;
+                            }
+                            __nanosleep(sleep);
+                            if (sleep < 1024) sleep <<= 1;
                         }
-                        __nanosleep(sleep);
-                        if (sleep < 1024) sleep <<= 1;
                     }
                 }
             }
@@ -1041,6 +1086,8 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring(RingPla
         }
         __syncthreads();
         if (s_go == 0) break;
+        const int s_rel = s_dec[0], j = s_dec[1], tile = s_dec[2];
+        const long long s_abs = sB.step + s_rel;
         if (s_go == 1)
             run_unit<PREC, true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
         __threadfence();
