@@ -387,7 +387,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": None if tpa is None else tpa * spec.n_atoms * args.md_steps,
-                "kernel": "k_ring<1> (mixed)",
+                "kernel": "k_ring_mixed (warp-level ring, mixed form)",
                 "counted": f"{FLOPS_PER_PAIR} flops x {PAIRS_PER_ATOM(spec.rho):.2f} directed "
                            f"in-cutoff pairs per atom-step",
                 "peak_note": "FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz"}

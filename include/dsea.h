@@ -81,7 +81,8 @@ typedef struct {
     int tile_y;        /* home cells per work unit along y; 0 = automatic */
     int tile_z;        /* home cells per work unit along z; 0 = automatic */
     int cell_capacity; /* atom slots per cell; 0 = from the density */
-    int ctas;          /* persistent stages (CTAs) for the ring; 0 = all that fit */
+    int ctas;          /* CTAs of a ring launch (one stage each in the FP64 form, one per
+                          warp in the mixed form); 0 = all that fit */
 } dsea_params;
 
 /* A box as the caller describes it (Sec. 4: cubic volume of edge b, but any

@@ -271,6 +271,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
         hb.lc[d] = L[d] / hb.nc[d];
         hb.inv_lc[d] = 1.0 / hb.lc[d];
         hb.lcf[d] = (float)hb.lc[d];
+        hb.inv_lcf[d] = 1.0f / hb.lcf[d];
     }
     hb.n_cells = (int64_t)hb.nc[0] * hb.nc[1] * hb.nc[2];
     if (hb.n_cells >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
@@ -299,7 +300,8 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     hb.w_is_sync = 1;
     hb.withhold_slice = -1;
     hb.wait_limit_ns = 5000000000LL;   // 5 s
-    // work-unit shape: requested, cached by the autotuner, or 4 x 4 cells
+    // work-unit shape: requested, cached by the autotuner, or a default (mixed
+    // form: 2 x 4 home cells per warp; FP64 form: 4 x 4 cells per CTA)
     int ty = p.tile_y, tz = p.tile_z;
     if (ty == 0 || tz == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -308,7 +310,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
             ty = it->second.first;
             tz = it->second.second;
         } else {
-            ty = ty ? ty : 4;
+            ty = ty ? ty : (p.precision == DSEA_MIXED ? 2 : 4);
             tz = tz ? tz : 4;
         }
     }
@@ -727,14 +729,19 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
             release();
             return DSEA_ERR_CUDA;
         }
-        static const int cand[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
+        // candidate unit shapes: mixed units are one warp's, FP64 units one CTA's
+        static const int cand_mixed[][2] = {{1, 2}, {2, 2}, {1, 4}, {2, 4}, {3, 3}, {4, 4}};
+        static const int cand_f64[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
+        const bool tune_mixed = hb.precision == 1;
+        const int n_cand = tune_mixed ? 6 : 8;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best_ms = 1e30f;
         const int sched = b->params.schedule;
         const BoxDev saved = hb;
-        for (const auto &c : cand) {
+        for (int ci = 0; ci < n_cand; ++ci) {
+            const int *c = tune_mixed ? cand_mixed[ci] : cand_f64[ci];
             BoxDev trial = saved;
             if (!apply_tile(trial, b->mean_cap, c[0], c[1])) continue;
             if (trial.tile_y != c[0] || trial.tile_z != c[1]) continue;   // clipped duplicate

@@ -33,6 +33,7 @@ struct BoxDev {
     double lc[3];
     double inv_lc[3];
     float lcf[3];
+    float inv_lcf[3];   // 1 / lcf, rounded
     int nc[3];
     int n_slices;
     int cps;

@@ -1,26 +1,26 @@
 // dsea_kernels.cu -- sm_103a kernels of the slice-streamed LJ NVE step.
 //
-// One work unit = all home cells of one slice (its cps cell layers along x)
-// within a tile_y x tile_z block of cells in (y, z).  A unit
-//   1. stages the counts of its neighbourhood cells (home cells plus one cell
-//      layer around them, periodic) and an exclusive scan of them,
-//   2. stages the atoms of those cells into shared memory, each cell sorted
-//      by atom id (so every sum below runs in an order fixed by the state
-//      alone: the same whatever the unit shape, launch form or batch),
-//   3. computes, warp per home cell, the force on each home atom from the 27
-//      neighbour cells (Algorithm 1's first loop, Sec. 4.1 "md_v3a"),
-//   4. (INTEGRATE) kicks and drifts each home atom (Algorithm 1's second and
-//      third loops, "md_v3aa" / "md_v3b") and appends it to the cell it
-//      moved to in the next-step buffer, which may belong to slice j-1, j or
-//      j+1 (O_out = 1, Sec. 4); warp-aggregated atomics reserve the slots,
-//   5. (OBS) reduces U, W and KE of its home atoms in FP64 ("stat_collect").
+// A work unit is the home cells of one slice (its cps cell layers along x)
+// within a tile_y x tile_z block of cells in (y, z).  For every home cell the
+// step computes the force on each home atom from the 27 neighbour cells
+// (Algorithm 1's first loop, Sec. 4.1 "md_v3a"), then kicks and drifts the
+// atom (Algorithm 1's second and third loops, "md_v3aa" / "md_v3b") and
+// writes it to the cell it moved to in the next-step buffer, which may belong
+// to slice j-1, j or j+1 (O_out = 1, Sec. 4).  Every per-atom sum runs in an
+// order fixed by the box state alone (neighbour cells in a fixed order, each
+// cell's atoms in its canonical order), so results do not depend on the unit
+// shape, the launch form or the batch.
 //
-// The FP64 form evaluates pairs on absolute positions and keeps velocities in
-// FP64.  The mixed form evaluates pairs in packed FP32x2 arithmetic on FP32
-// coordinates relative to each atom's cell centre and keeps velocities in
-// FP32; FP64 is kept for the absolute positions, the position update and
-// every reduction (FP64 issues at a small fraction of the FP32 rate on this
-// GPU, so the mixed form spends about a dozen FP64 operations per atom-step).
+// The FP64 form runs a unit per CTA: it stages the unit's neighbourhood into
+// shared memory as absolute positions and evaluates pairs in FP64.
+//
+// The mixed form runs a unit per warp: for each home cell the warp gathers
+// the 27-cell neighbourhood into a flat list of FP32 coordinates in the home
+// cell's centred frame and evaluates pairs in packed FP32x2 arithmetic;
+// velocities are FP32; the absolute positions, their update and every
+// reduction stay FP64 (FP64 issues at a small fraction of the FP32 rate on
+// this GPU, so the mixed form spends about a dozen FP64 operations per
+// atom-step).
 #include "dsea_internal.h"
 
 namespace dsea {
@@ -28,7 +28,6 @@ namespace dsea {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPrefBytes = 32 * (3 * 8 + 3 * 4);   // per warp: own atoms' r (FP64) and v (FP32)
 
 __device__ __forceinline__ void set_error(int *err, int code)
 {
@@ -61,19 +60,6 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Asynchronous 16-byte global -> shared copy that bypasses L1 (.cg), so data
-// other CTAs wrote earlier in the same persistent launch is always seen (L1
-// is not kept coherent with other SMs' writes).  Both addresses 16-B aligned.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // floor(a / d) for 0 <= a < 2^22 through the FP32 reciprocal inv_d = 1/d
@@ -89,12 +75,12 @@ __device__ __forceinline__ float inv_of(int d)
     return __frcp_rn((float)d);
 }
 
-// Shared-memory carve-up of one unit.
+// Shared-memory carve-up of one FP64 unit.
 struct Layout {
-    size_t cnt, nst, start, gcell, atoms, id, slot, scr, ctab, tab, red, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, id, slot, scr, red, ctr, total;
 };
 
-__host__ __device__ inline Layout make_layout(int precision, int staged_cells, int smem_atoms)
+__host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
 {
     Layout L;
     size_t o = 0;
@@ -103,23 +89,13 @@ __host__ __device__ inline Layout make_layout(int precision, int staged_cells, i
     L.start = o; o += sizeof(int) * (staged_cells + 1);
     L.gcell = o; o += sizeof(int) * staged_cells;
     o = align16(o);
-    L.atoms = o;
-    if (precision == 1) {
-        o += sizeof(float4) * smem_atoms;       // x, y, z, id bits
-        L.id = 0;
-    } else {
-        o += 3 * sizeof(double) * smem_atoms;   // x[], y[], z[]
-        L.id = o;
-        o += sizeof(int) * smem_atoms;
-    }
-    L.slot = o; o += sizeof(int) * smem_atoms;
+    L.atoms = o; o += 3 * sizeof(double) * smem_atoms;   // x[], y[], z[]
+    L.id = o;    o += sizeof(int) * smem_atoms;
+    L.slot = o;  o += sizeof(int) * smem_atoms;
     o = align16(o);
-    L.scr = o;                                  // FP64: partial sums; mixed: r/v prefetch
-    o += precision == 1 ? (size_t)kWarps * kPrefBytes : sizeof(double) * kThreads * 5;
-    L.ctab = o; o += sizeof(double) * kWarps * 9;   // mixed: neighbour cell centres
-    L.tab = o;  o += sizeof(int2) * kWarps * 32;     // mixed: neighbour cell table per warp
-    L.red = o;  o += sizeof(double) * kWarps * 3;
-    L.ctr = o;  o += 16;
+    L.scr = o;   o += sizeof(double) * kThreads * 5;     // partial sums of split home atoms
+    L.red = o;   o += sizeof(double) * kWarps * 3;
+    L.ctr = o;   o += 16;
     L.total = align16(o);
     return L;
 }
@@ -163,10 +139,12 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c)
 
 __device__ __forceinline__ float2 f2splat(float x) { return make_float2(x, x); }
 
-// Unrolling of the 27-cell stencil loops of the mixed force routine.
-#ifndef DSEA_CELL_UNROLL
-#define DSEA_CELL_UNROLL _Pragma("unroll 1")
+// Unrolling of the mixed form's pair loop over the neighbour list.
+#ifndef DSEA_PAIR_UNROLL_N
+#define DSEA_PAIR_UNROLL_N 2
 #endif
+#define DSEA_PRAGMA(x) _Pragma(#x)
+#define DSEA_UNROLL(n) DSEA_PRAGMA(unroll n)
 
 // 0 < r2 <= rc2 on the bit patterns of non-negative floats (excludes the atom
 // itself, at r2 == 0, in the same test as the cutoff).
@@ -226,116 +204,6 @@ __device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const fl
         u.y = in1 ? u.y : 0.f;
         a.u = f2add(a.u, u);
         a.w = f2fma(R2, FS, a.w);
-    }
-}
-
-// Mixed-form forces on the atoms of one home cell chunk (nin <= 32 atoms
-// starting at staged index `base`), warp-wide.  Each lane carries two home
-// atoms and evaluates both against the same staged neighbour with packed
-// FP32x2 arithmetic; lanes split each neighbour cell's atoms by stride ns.
-// The ns partial sums of an atom are then combined in split order, so each
-// atom's force is summed in an order fixed by the box state.  Lane l < nin
-// returns the totals of atom base + l.
-template <bool OBS>
-__device__ __forceinline__ void packed_forces(const BoxDev &B, const float4 *s_q, const int *s_start,
-                                              const int *s_cnt, int2 *tab, int hx, int hy, int hz, int EY,
-                                              int EZ, int base, int nin, int lane, float &fx, float &fy,
-                                              float &fz, float &uu, float &ww)
-{
-    const int np = (nin + 1) >> 1;
-    const float inv_np = inv_of(np);
-    const int ns = qdiv(32, inv_np);
-    const int g = qdiv(lane, inv_np), pi = lane - g * np;
-    const bool act = g < ns;
-    const int a0 = 2 * pi, a1 = min(2 * pi + 1, nin - 1);   // odd nin: the last pair repeats an atom
-    Acc2 acc = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)};
-    // table of the 26 neighbour cells: staged start and prefix of the counts
-    // (lane 26 holds the total), so the cells read as one list
-    {
-        int cs = 0, cn = 0;
-        if (lane < 26) {
-            const int kk = lane + (lane >= 13 ? 1 : 0);
-            const int ox = kk / 9 - 1, oy = (kk / 3) % 3 - 1, oz = kk % 3 - 1;
-            const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
-            cs = s_start[kn];
-            cn = s_cnt[kn];
-        }
-        int incl = cn;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane <= 26) tab[lane] = make_int2(cs, incl - cn);
-        __syncwarp();
-    }
-    if (act) {
-        const float4 q0 = s_q[base + a0], q1 = s_q[base + a1];
-        const float2 X = make_float2(q0.x, q1.x), Y = make_float2(q0.y, q1.y), Z = make_float2(q0.z, q1.z);
-        const unsigned rcb = __float_as_uint(B.rc2f);
-        const float rc2f = B.rc2f, ush = B.ushiftf;
-        // the home cell (it holds the atoms themselves: exact test), split by stride
-        {
-            const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
-            const float4 *qc = s_q + s_start[kh];
-            const int cn = s_cnt[kh];
-            for (int t = g; t < cn; t += ns) pair2<true, OBS>(X, Y, Z, qc[t], rc2f, rcb, ush, acc);
-        }
-        // the 26 neighbour cells as one list, an equal contiguous share per split
-        const int M = tab[26].y;
-        const int chunk = qdiv(M + ns - 1, inv_of(ns));
-        int t = g * chunk;
-        const int e = min(M, t + chunk);
-        if (t < e) {
-            int lo = 0, hi = 25;   // the cell holding list position t
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (tab[mid].y <= t) lo = mid; else hi = mid - 1;
-            }
-            int k = lo;
-            int end = tab[k + 1].y, off = tab[k].x - tab[k].y;
-            float2 XS, YS, ZS;
-            auto frame = [&](int kc) {   // home atoms in neighbour cell kc's centred frame
-                const int kk = kc + (kc >= 13 ? 1 : 0);
-                XS = f2sub(X, f2splat((float)(kk / 9 - 1) * B.lcf[0]));
-                YS = f2sub(Y, f2splat((float)((kk / 3) % 3 - 1) * B.lcf[1]));
-                ZS = f2sub(Z, f2splat((float)(kk % 3 - 1) * B.lcf[2]));
-            };
-            frame(k);
-            for (; t < e; ++t) {
-                while (t == end) {   // next non-empty cell
-                    ++k;
-                    end = tab[k + 1].y;
-                    off = tab[k].x - tab[k].y;
-                    frame(k);
-                }
-                if (OBS) pair2<true, true>(XS, YS, ZS, s_q[off + t], rc2f, rcb, ush, acc);
-                else pair2<false, false>(XS, YS, ZS, s_q[off + t], rc2f, rcb, ush, acc);
-            }
-        }
-    }
-    const float2 FX = acc.fx, FY = acc.fy, FZ = acc.fz, UU = acc.u, WW = acc.w;
-    // combine the ns partials of each atom pair into lane pi, in split order
-    float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
-    for (int gg = 1; gg < ns; ++gg) {
-        const int src = pi + gg * np;   // < ns * np <= 32
-        SX.x += __shfl_sync(kFull, FX.x, src); SX.y += __shfl_sync(kFull, FX.y, src);
-        SY.x += __shfl_sync(kFull, FY.x, src); SY.y += __shfl_sync(kFull, FY.y, src);
-        SZ.x += __shfl_sync(kFull, FZ.x, src); SZ.y += __shfl_sync(kFull, FZ.y, src);
-        if (OBS) {
-            SU.x += __shfl_sync(kFull, UU.x, src); SU.y += __shfl_sync(kFull, UU.y, src);
-            SW.x += __shfl_sync(kFull, WW.x, src); SW.y += __shfl_sync(kFull, WW.y, src);
-        }
-    }
-    // atom l (l < nin) is half l & 1 of the pair held by lane l >> 1
-    const int from = (lane >> 1) < np ? (lane >> 1) : 0;
-    const bool hi = lane & 1;
-    float t0, t1;
-    t0 = __shfl_sync(kFull, SX.x, from); t1 = __shfl_sync(kFull, SX.y, from); fx = hi ? t1 : t0;
-    t0 = __shfl_sync(kFull, SY.x, from); t1 = __shfl_sync(kFull, SY.y, from); fy = hi ? t1 : t0;
-    t0 = __shfl_sync(kFull, SZ.x, from); t1 = __shfl_sync(kFull, SZ.y, from); fz = hi ? t1 : t0;
-    if (OBS) {
-        t0 = __shfl_sync(kFull, SU.x, from); t1 = __shfl_sync(kFull, SU.y, from); uu = hi ? t1 : t0;
-        t0 = __shfl_sync(kFull, SW.x, from); t1 = __shfl_sync(kFull, SW.y, from); ww = hi ? t1 : t0;
     }
 }
 
@@ -492,15 +360,28 @@ __device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, co
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
-// The work unit (see file header).  s_abs: absolute step of the input state.
-template <int PREC, bool INTEGRATE, bool OBS>
-__device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool first_step,
-                         int unit_id, char *smem)
+// The FP64 work unit.  One CTA = all home cells of one slice (its cps cell
+// layers along x) within a tile_y x tile_z block of cells in (y, z).  It
+//   1. stages the counts of its neighbourhood cells (home cells plus one cell
+//      layer around them, periodic) and an exclusive scan of them,
+//   2. stages the atoms of those cells into shared memory in each cell's
+//      canonical order (stayers in slot order, then arrivals by atom id), as
+//      absolute positions shifted to the periodic image next to the unit,
+//   3. computes, warp per home cell, the force on each home atom from the 27
+//      neighbour cells (Algorithm 1's first loop, Sec. 4.1 "md_v3a"),
+//   4. (INTEGRATE) kicks and drifts each home atom (Algorithm 1's second and
+//      third loops) and writes it to the cell it moved to in the next-step
+//      buffer, which may belong to slice j-1, j or j+1 (O_out = 1, Sec. 4),
+//   5. (OBS) reduces U, W and KE of its home atoms in FP64 ("stat_collect").
+// s_abs: absolute step of the input state.
+template <bool INTEGRATE, bool OBS>
+__device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, bool first_step,
+                             int unit_id, char *smem)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = (int)(s_abs & 1);
     const unsigned tag = (unsigned)(s_abs + 1);
-    const Layout Ly = make_layout(PREC, B.staged_cells, B.smem_atoms);
+    const Layout Ly = make_layout(B.staged_cells, B.smem_atoms);
     int *s_cnt = reinterpret_cast<int *>(smem + Ly.cnt);
     int *s_nst = reinterpret_cast<int *>(smem + Ly.nst);
     int *s_start = reinterpret_cast<int *>(smem + Ly.start);
@@ -508,7 +389,6 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
     double *s_red = reinterpret_cast<double *>(smem + Ly.red);
     int *s_ctr = reinterpret_cast<int *>(smem + Ly.ctr);
-    float4 *s_q = reinterpret_cast<float4 *>(smem + Ly.atoms);
     double *s_x = reinterpret_cast<double *>(smem + Ly.atoms);
     double *s_y = s_x + B.smem_atoms;
     double *s_z = s_y + B.smem_atoms;
@@ -569,50 +449,27 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         return;
     }
     // 3. stage atoms in each cell's canonical order: the stayers (front
-    // slots) as they are, then the arrivals (back slots) ordered by atom id.
-    // Mixed form: every warp issues asynchronous 16-byte copies of its cells'
-    // two slot ranges and moves on; after one wait and barrier, each cell's
-    // arrivals are ordered in place.  FP64 form: lanes load their atoms (L2)
-    // and write them to their place.
+    // slots) as they are, then the arrivals (back slots) ordered by atom id
     const long long S = B.n_slots;
-    if (PREC == 1) {
-        for (int k = warp; k < n_staged; k += kWarps) {
-            const int c = s_cnt[k];
-            if (c == 0) continue;
-            const int n_s = s_nst[k], n_a = c - n_s;
-            const long long base = (long long)s_gcell[k] * B.cap;
-            const int st = s_start[k];
-            for (int a = lane; a < c; a += 32) {
-                const long long src = a < n_s ? base + a : base + B.cap - n_a + (a - n_s);
-                cp_async16(s_q + st + a, B.q[p] + src);
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
     for (int k = warp; k < n_staged; k += kWarps) {
         const int c = s_cnt[k];
         if (c == 0) continue;
         const int n_s = s_nst[k], n_a = c - n_s;
         const long long base = (long long)s_gcell[k] * B.cap;
         const int st = s_start[k];
-        double shx = 0.0, shy = 0.0, shz = 0.0;
-        if (PREC == 0) {   // periodic image shift of this staged cell
-            const int lx = qdiv(k, inv_eyez), rem = k - lx * EY * EZ, ly = qdiv(rem, inv_ez), lz = rem - ly * EZ;
-            const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
-            shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
-            shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
-            shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
-        }
+        // periodic image shift of this staged cell
+        const int lx = qdiv(k, inv_eyez), rem = k - lx * EY * EZ, ly = qdiv(rem, inv_ez), lz = rem - ly * EZ;
+        const int ux = x0 - 1 + lx, uy = y0 - 1 + ly, uz = z0 - 1 + lz;
+        const double shx = ux < 0 ? -B.L[0] : (ux >= B.nc[0] ? B.L[0] : 0.0);
+        const double shy = uy < 0 ? -B.L[1] : (uy >= B.nc[1] ? B.L[1] : 0.0);
+        const double shz = uz < 0 ? -B.L[2] : (uz >= B.nc[2] ? B.L[2] : 0.0);
         for (int a = lane; a < n_s; a += 32) {
             const long long slot = base + a;
             s_slot[st + a] = (int)slot;
-            if (PREC == 0) {
-                s_x[st + a] = __ldcg(B.r[p] + slot) + shx;
-                s_y[st + a] = __ldcg(B.r[p] + S + slot) + shy;
-                s_z[st + a] = __ldcg(B.r[p] + 2 * S + slot) + shz;
-                s_id[st + a] = __ldcg(B.id[p] + slot);
-            }
+            s_x[st + a] = __ldcg(B.r[p] + slot) + shx;
+            s_y[st + a] = __ldcg(B.r[p] + S + slot) + shy;
+            s_z[st + a] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+            s_id[st + a] = __ldcg(B.id[p] + slot);
         }
         if (n_a == 0) continue;
         // arrivals: rank by atom id among themselves (up to 4 per lane)
@@ -624,57 +481,42 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         }
         const int nm = (n_a + 31) >> 5;
         int idm[4];
-        float4 qm[4];
         double xm[4], ym[4], zm[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int a = lane + 32 * m;
             idm[m] = 0x7fffffff;
             if (m < nm && a < n_a) {
-                if (PREC == 1) {
-                    qm[m] = s_q[fa + a];
-                    idm[m] = __float_as_int(qm[m].w);
-                } else {
-                    const long long slot = abase + a;
-                    xm[m] = __ldcg(B.r[p] + slot) + shx;
-                    ym[m] = __ldcg(B.r[p] + S + slot) + shy;
-                    zm[m] = __ldcg(B.r[p] + 2 * S + slot) + shz;
-                    idm[m] = __ldcg(B.id[p] + slot);
-                }
+                const long long slot = abase + a;
+                xm[m] = __ldcg(B.r[p] + slot) + shx;
+                ym[m] = __ldcg(B.r[p] + S + slot) + shy;
+                zm[m] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+                idm[m] = __ldcg(B.id[p] + slot);
             }
         }
         int rk[4] = {0, 0, 0, 0};
-        if (nm == 1) {
-            for (int t = 0; t < n_a; ++t) rk[0] += (__shfl_sync(kFull, idm[0], t) < idm[0]) ? 1 : 0;
-        } else {
 #pragma unroll
-            for (int mb = 0; mb < 4; ++mb) {
-                if (mb < nm) {
-                    const int lim = min(32, n_a - 32 * mb);
-                    for (int t = 0; t < lim; ++t) {
-                        const int o = __shfl_sync(kFull, idm[mb], t);
+        for (int mb = 0; mb < 4; ++mb) {
+            if (mb < nm) {
+                const int lim = min(32, n_a - 32 * mb);
+                for (int t = 0; t < lim; ++t) {
+                    const int o = __shfl_sync(kFull, idm[mb], t);
 #pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            if (m < nm) rk[m] += (o < idm[m]) ? 1 : 0;
-                    }
+                    for (int m = 0; m < 4; ++m)
+                        if (m < nm) rk[m] += (o < idm[m]) ? 1 : 0;
                 }
             }
         }
-        __syncwarp();   // every lane has read the arrivals before any writes
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int a = lane + 32 * m;
             if (m < nm && a < n_a) {
                 const int dst = fa + rk[m];
                 s_slot[dst] = (int)(abase + a);
-                if (PREC == 1) {
-                    s_q[dst] = qm[m];
-                } else {
-                    s_x[dst] = xm[m];
-                    s_y[dst] = ym[m];
-                    s_z[dst] = zm[m];
-                    s_id[dst] = idm[m];
-                }
+                s_x[dst] = xm[m];
+                s_y[dst] = ym[m];
+                s_z[dst] = zm[m];
+                s_id[dst] = idm[m];
             }
         }
     }
@@ -689,7 +531,6 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
     const unsigned tag_next = tag + 1u;
     const double dt = B.dt;
     const double kick = first_step ? 0.5 * dt : dt;
-    const float dtf = (float)dt;
     int h = OBS ? warp : 0;
     if (!OBS) {
         if (lane == 0) h = atomicAdd(s_ctr, 1);
@@ -700,17 +541,8 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
         const int kh = ((hx + 1) * EY + (hy + 1)) * EZ + (hz + 1);
         const int n_i = s_cnt[kh];
         const int hs = s_start[kh];
-        const int cg[3] = {x0 + hx, y0 + hy, z0 + hz};   // home cell (within the box)
         const long long hcell = s_gcell[kh];
         int n_stay = 0;   // atoms of this cell that stay in it, written to its front slots in order
-        double *ctab = reinterpret_cast<double *>(smem + Ly.ctab) + warp * 9;
-        if (PREC == 1) {
-            if (lane < 9) {
-                const int ax = lane / 3, o = lane - 3 * (lane / 3) - 1;
-                ctab[lane] = ((double)(cg[ax] + o) + 0.5) * B.lc[ax];
-            }
-            __syncwarp();
-        }
         for (int ib = 0; ib < n_i; ib += 32) {
             const int nin = min(32, n_i - ib);
             const float inv_nin = inv_of(nin);
@@ -721,154 +553,77 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
             const bool own = lane < nin;
             long long slot = 0;
             if (own) slot = s_slot[is];
-            if (PREC == 1) {
-                // prefetch the home cell's positions (FP64) and velocities (FP32)
-                // in slot order, 16-byte copies, while the forces are computed
-                // (cells of up to 32 atoms; larger ones are read after)
-                char *pref = smem + Ly.scr + (size_t)warp * kPrefBytes;
-                double *pr = reinterpret_cast<double *>(pref);          // [3][32]
-                float *pv = reinterpret_cast<float *>(pref + 32 * 3 * 8);  // [3][32]
-                const long long hbase = (long long)s_gcell[kh] * B.cap;
-                const int n_front = s_nst[kh];   // stayers: slots [0, n_front); arrivals at the back
-                const bool pf = n_front <= 32;
-                if (pf) {
-                    const int n2 = (n_front + 1) >> 1, n4 = (n_front + 3) >> 2;
-                    for (int d = 0; d < 3; ++d) {
-                        if (lane < n2) cp_async16(pr + 32 * d + 2 * lane, B.r[p] + d * S + hbase + 2 * lane);
-                        if (lane < n4) cp_async16(pv + 32 * d + 4 * lane, B.vf[p] + d * S + hbase + 4 * lane);
-                    }
-                }
-                float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
-                packed_forces<OBS>(B, s_q, s_start, s_cnt, reinterpret_cast<int2 *>(smem + Ly.tab) + warp * 32,
-                                   hx, hy, hz, EY, EZ, hs + ib, nin, lane, fx,
-                                   fy, fz, uu, ww);
-                cp_async_wait_all();
+            Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
+            if (act) {
+                const double xi = s_x[is], yi = s_y[is], zi = s_z[is];
+                for (int ox = -1; ox <= 1; ++ox)
+                    for (int oy = -1; oy <= 1; ++oy)
+                        for (int oz = -1; oz <= 1; ++oz) {
+                            const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+                            const int cs = s_start[kn], cn = s_cnt[kn];
+                            for (int t = g; t < cn; t += ns)
+                                pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t], B.rc2,
+                                              B.ushift, a64);
+                        }
+            }
+            // combine the ns partial sums of each home atom in split order
+            double fx = a64.fx, fy = a64.fy, fz = a64.fz, uu = a64.u, ww = a64.w;
+            if (ns > 1) {
+                double *scr = reinterpret_cast<double *>(smem + Ly.scr) + warp * 32 * 5;
+                scr[lane * 5 + 0] = a64.fx; scr[lane * 5 + 1] = a64.fy; scr[lane * 5 + 2] = a64.fz;
+                scr[lane * 5 + 3] = a64.u;  scr[lane * 5 + 4] = a64.w;
                 __syncwarp();
-                int aid = 0;
-                double rr[3] = {0.0, 0.0, 0.0};
-                float vv[3] = {0.f, 0.f, 0.f};
-                float4 qo = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g == 0) {
+                    for (int gg = 1; gg < ns; ++gg) {
+                        const int o = (li + gg * nin) * 5;
+                        fx += scr[o]; fy += scr[o + 1]; fz += scr[o + 2]; uu += scr[o + 3]; ww += scr[o + 4];
+                    }
+                }
+                __syncwarp();
+            }
+            int aid = 0;
+            double rx = 0, ry = 0, rz = 0, vx = 0, vy = 0, vz = 0;
+            if (own) {
+                aid = s_id[is];
+                rx = __ldcg(B.r[p] + slot);
+                ry = __ldcg(B.r[p] + S + slot);
+                rz = __ldcg(B.r[p] + 2 * S + slot);
+                vx = __ldcg(B.v[p] + slot);
+                vy = __ldcg(B.v[p] + S + slot);
+                vz = __ldcg(B.v[p] + 2 * S + slot);
+                if (OBS) {
+                    const double hk = first_step ? 0.0 : 0.5 * dt;
+                    const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
+                    red_u += 0.5 * uu;
+                    red_w += 0.5 * ww;
+                    red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
+                    if (!INTEGRATE) {
+                        const long long o = 3LL * aid;
+                        B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
+                        B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
+                        B.out_r[o] = rx; B.out_r[o + 1] = ry; B.out_r[o + 2] = rz;
+                    }
+                }
+            }
+            if (INTEGRATE) {
+                long long dest = 0;
                 if (own) {
-                    qo = s_q[is];
-                    aid = __float_as_int(qo.w);
-                    for (int d = 0; d < 3; ++d) {
-                        const int a = (int)(slot - hbase);
-                        const bool hit = pf && a < n_front;
-                        rr[d] = hit ? pr[32 * d + a] : __ldcg(B.r[p] + d * S + slot);
-                        vv[d] = hit ? pv[32 * d + a] : __ldcg(B.vf[p] + d * S + slot);
-                    }
-                    if (OBS) {
-                        // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
-                        const float hk = first_step ? 0.f : 0.5f * dtf;
-                        const float sx = fmaf(hk, fx, vv[0]), sy = fmaf(hk, fy, vv[1]), sz = fmaf(hk, fz, vv[2]);
-                        red_u += 0.5 * (double)uu;
-                        red_w += 0.5 * (double)ww;
-                        red_k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
-                        if (!INTEGRATE) {
-                            const long long o = 3LL * aid;
-                            B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
-                            B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
-                            B.out_r[o] = rr[0]; B.out_r[o + 1] = rr[1]; B.out_r[o + 2] = rr[2];
-                        }
-                    }
+                    vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
+                    vy += kick * fy;
+                    vz += kick * fz;
+                    rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
+                    ry = wrap_coord(ry + vy * dt, B.L[1]);
+                    rz = wrap_coord(rz + vz * dt, B.L[2]);
+                    const int cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
+                    const int cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
+                    const int cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
+                    const int dj = qdiv(cx, inv_cps) - j;
+                    const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
+                    if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
+                    dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
                 }
-                __syncwarp();   // the prefetch area is reused by the next chunk
-                if (INTEGRATE) {
-                    long long dest = 0;
-                    float qn[3] = {0.f, 0.f, 0.f};
-                    if (own) {
-                        const float kf = first_step ? 0.5f * dtf : dtf;
-                        vv[0] = fmaf(kf, fx, vv[0]);   // v(t + dt/2) = v(t - dt/2) + F dt
-                        vv[1] = fmaf(kf, fy, vv[1]);
-                        vv[2] = fmaf(kf, fz, vv[2]);
-                        const float q3[3] = {qo.x, qo.y, qo.z};
-                        int c3[3];
-                        for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
-                            c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], ctab + 3 * d, B.lc[d],
-                                              1.0f / B.lcf[d], B.L[d], B.nc[d], qn[d]);
-                        const int dj = qdiv(c3[0], inv_cps) - j;
-                        const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
-                        if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
-                        dest = ((long long)c3[0] * B.nc[1] + c3[1]) * B.nc[2] + c3[2];
-                    }
-                    const long long slot_n = place_slot(B, pn, hcell, dest, own, tag_next, lane, n_stay);
-                    if (slot_n >= 0)
-                        store_mixed(B, pn, slot_n, aid, rr[0], rr[1], rr[2], vv[0], vv[1], vv[2], qn[0], qn[1],
-                                    qn[2]);
-                }
-            } else {
-                Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
-                if (act) {
-                    const double xi = s_x[is], yi = s_y[is], zi = s_z[is];
-                    for (int ox = -1; ox <= 1; ++ox)
-                        for (int oy = -1; oy <= 1; ++oy)
-                            for (int oz = -1; oz <= 1; ++oz) {
-                                const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
-                                const int cs = s_start[kn], cn = s_cnt[kn];
-                                for (int t = g; t < cn; t += ns)
-                                    pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t],
-                                                  B.rc2, B.ushift, a64);
-                            }
-                }
-                // combine the ns partial sums of each home atom in split order
-                double fx = a64.fx, fy = a64.fy, fz = a64.fz, uu = a64.u, ww = a64.w;
-                if (ns > 1) {
-                    double *scr = reinterpret_cast<double *>(smem + Ly.scr) + warp * 32 * 5;
-                    scr[lane * 5 + 0] = a64.fx; scr[lane * 5 + 1] = a64.fy; scr[lane * 5 + 2] = a64.fz;
-                    scr[lane * 5 + 3] = a64.u;  scr[lane * 5 + 4] = a64.w;
-                    __syncwarp();
-                    if (g == 0) {
-                        for (int gg = 1; gg < ns; ++gg) {
-                            const int o = (li + gg * nin) * 5;
-                            fx += scr[o]; fy += scr[o + 1]; fz += scr[o + 2]; uu += scr[o + 3]; ww += scr[o + 4];
-                        }
-                    }
-                    __syncwarp();
-                }
-                int aid = 0;
-                double rx = 0, ry = 0, rz = 0, vx = 0, vy = 0, vz = 0;
-                if (own) {
-                    aid = s_id[is];
-                    rx = __ldcg(B.r[p] + slot);
-                    ry = __ldcg(B.r[p] + S + slot);
-                    rz = __ldcg(B.r[p] + 2 * S + slot);
-                    vx = __ldcg(B.v[p] + slot);
-                    vy = __ldcg(B.v[p] + S + slot);
-                    vz = __ldcg(B.v[p] + 2 * S + slot);
-                    if (OBS) {
-                        const double hk = first_step ? 0.0 : 0.5 * dt;
-                        const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
-                        red_u += 0.5 * uu;
-                        red_w += 0.5 * ww;
-                        red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
-                        if (!INTEGRATE) {
-                            const long long o = 3LL * aid;
-                            B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
-                            B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
-                            B.out_r[o] = rx; B.out_r[o + 1] = ry; B.out_r[o + 2] = rz;
-                        }
-                    }
-                }
-                if (INTEGRATE) {
-                    long long dest = 0;
-                    if (own) {
-                        vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
-                        vy += kick * fy;
-                        vz += kick * fz;
-                        rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
-                        ry = wrap_coord(ry + vy * dt, B.L[1]);
-                        rz = wrap_coord(rz + vz * dt, B.L[2]);
-                        const int cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
-                        const int cy = cell_of(ry, B.inv_lc[1], B.nc[1]);
-                        const int cz = cell_of(rz, B.inv_lc[2], B.nc[2]);
-                        const int dj = qdiv(cx, inv_cps) - j;
-                        const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
-                        if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
-                        dest = ((long long)cx * B.nc[1] + cy) * B.nc[2] + cz;
-                    }
-                    const long long slot_n = place_slot(B, pn, hcell, dest, own, tag_next, lane, n_stay);
-                    if (slot_n >= 0) store_f64(B, pn, slot_n, aid, rx, ry, rz, vx, vy, vz);
-                }
+                const long long slot_n = place_slot(B, pn, hcell, dest, own, tag_next, lane, n_stay);
+                if (slot_n >= 0) store_f64(B, pn, slot_n, aid, rx, ry, rz, vx, vy, vz);
             }
             __syncwarp();
         }
@@ -907,6 +662,339 @@ __device__ void run_unit(const BoxDev &B, int j, int tile, long long s_abs, bool
             B.unit_obs[3LL * unit_id + 2] = k;
         }
     }
+}
+
+// ---- mixed form: one warp per home cell ----------------------------------------
+//
+// A warp gathers the 27-cell neighbourhood of its home cell straight from the
+// state in L2 into a flat list in its own shared memory, every neighbour's
+// FP32 coordinates shifted into the home cell's centred frame (home cell
+// first, then the 26 others in (ox, oy, oz) order), and evaluates its home
+// atoms against that list with packed FP32x2 arithmetic, then kicks, drifts
+// and rebins them.  A neighbourhood longer than the list is processed in
+// windows of kListAtoms.  There is no unit-wide staging, so warps never wait
+// for each other inside a unit.
+
+constexpr int kListAtoms = 352;   // list window (atoms) of one warp
+constexpr int kHomeMax = 128;     // largest cell capacity (slots of one home cell)
+
+// Per-warp shared memory of the mixed form.  The context fields are written
+// once per home cell and read back through volatile loads where they are
+// needed, so that no register holds them across the pair loop.
+struct WarpArea {
+    float4 list[kListAtoms];   // neighbour window: x, y, z in the home frame, atom id bits
+    int hslot[kHomeMax];       // slot of each home atom, in the cell's canonical order
+    double ctab[9];            // FP64 centres of home cells cg-1, cg, cg+1 per axis
+    long long s_abs;           // step of the input state
+    long long hcell;           // home cell
+    int j, tile, first;        // unit and first-step flag
+    int rel, box;              // ring: relative step and box of the unit
+    int hx, hy, hz;            // home cell coordinates
+    int n_home, total, built;  // home atoms, neighbourhood atoms, window held by the list
+    int n_stay;                // atoms that stayed in the home cell so far
+};
+
+// Lane c (< 27) of a warp describes one cell of the neighbourhood of home
+// cell (hx, hy, hz): lane 0 the home cell, lanes 1..26 the others.
+struct NbrCell {
+    int gc;           // global cell index
+    int n_s, n_a;     // stayers (front slots) and arrivals (back slots)
+    int pre;          // first list position of the cell
+    float sx, sy, sz; // shift of the cell's centre from the home cell's centre
+};
+
+__device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag, int hx, int hy, int hz,
+                                            int lane, int &total)
+{
+    NbrCell c = {0, 0, 0, 0, 0.f, 0.f, 0.f};
+    if (lane < 27) {
+        const int kk = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+        const int ox = kk / 9 - 1, oy = (kk / 3) % 3 - 1, oz = kk % 3 - 1;
+        const int gx = wrap_index(hx + ox, B.nc[0]), gy = wrap_index(hy + oy, B.nc[1]),
+                  gz = wrap_index(hz + oz, B.nc[2]);
+        const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
+        const unsigned long long ws = __ldcg(B.cnt[p] + gc), wa = __ldcg(B.arr[p] + gc);
+        int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;
+        int n_a = ((unsigned)(wa >> 32) == tag) ? (int)(unsigned)wa : 0;
+        if (n_s + n_a > B.cap) {   // the two ends met: the cell overflowed
+            set_error(B.err, kErrCapacity);
+            n_s = min(n_s, B.cap);
+            n_a = B.cap - n_s;
+        }
+        c.gc = gc;
+        c.n_s = n_s;
+        c.n_a = n_a;
+        c.sx = (float)ox * B.lcf[0];
+        c.sy = (float)oy * B.lcf[1];
+        c.sz = (float)oz * B.lcf[2];
+    }
+    const int n = c.n_s + c.n_a;
+    int incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    c.pre = incl - n;
+    total = __shfl_sync(kFull, incl, 31);
+    return c;
+}
+
+// Copy list positions [w0, w0 + kListAtoms) of the neighbourhood into the
+// warp's list (lane c copies its cell's share).  A cell's canonical order is
+// its stayers in slot order, then its arrivals ordered by atom id.  Home
+// cell entries also record their slot.
+__device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCell &c, int w0, int lane,
+                                             WarpArea &wa)
+{
+    if (lane < 27) {
+        const float4 *q = B.q[p];
+        const int w1 = w0 + kListAtoms;
+        const long long base = (long long)c.gc * B.cap;
+        // stayers: canonical position i = slot offset i
+        const int lo = max(0, w0 - c.pre), hi = min(c.n_s, w1 - c.pre);
+#pragma unroll 2
+        for (int i = lo; i < hi; ++i) {
+            const long long slot = base + i;
+            const float4 a = __ldcg(q + slot);
+            wa.list[c.pre + i - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
+            if (lane == 0) wa.hslot[i] = (int)slot;
+        }
+        // arrivals: slot cap-1-k holds the k-th arrival; order them by id
+        const long long abase = base + B.cap - c.n_a;
+        const int a0 = c.pre + c.n_s;
+        const int n_arr = (a0 < w1 && a0 + c.n_a > w0) ? c.n_a : 0;
+        for (int t = 0; t < n_arr; ++t) {
+            int r = 0;
+            const long long slot = abase + t;
+            const float4 a = __ldcg(q + slot);
+            if (c.n_a > 1) {
+                const int id = __float_as_int(a.w);
+                for (int u = 0; u < c.n_a; ++u)
+                    r += (__float_as_int(__ldcg(q + abase + u).w) < id) ? 1 : 0;
+            }
+            const int cp = a0 + r;   // canonical list position
+            if (cp >= w0 && cp < w1) {
+                wa.list[cp - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
+                if (lane == 0) wa.hslot[c.n_s + r] = (int)slot;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Forces on home atoms [ib, ib + nin) of the warp's home cell from the whole
+// neighbourhood (all windows), packed FP32x2: each lane carries two home
+// atoms, and the ns lane groups split each window's list into equal
+// contiguous shares (the home cell's entries, which include the atoms
+// themselves, by stride with the exact cutoff test).  The partial sums are
+// combined in group order, so each atom's force is summed in an order fixed
+// by the box state.  Lane l < nin returns the totals of home atom ib + l.
+template <bool OBS>
+__device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int ib, int lane, float &fx,
+                                            float &fy, float &fz, float &uu, float &ww)
+{
+    const volatile WarpArea &v = wa;
+    const int total = v.total, n_home = v.n_home;
+    const int nin = min(32, n_home - ib);
+    const int np = (nin + 1) >> 1;
+    const float inv_np = inv_of(np);
+    const int ns = qdiv(32, inv_np);
+    const int g = qdiv(lane, inv_np), pi = lane - g * np;
+    const bool act = g < ns;
+    Acc2 acc = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)};
+    float2 X = f2splat(0.f), Y = X, Z = X;
+    const int n_win = (total + kListAtoms - 1) / kListAtoms;
+    for (int w = 0; w < n_win; ++w) {
+        if (v.built != w) {   // only when the neighbourhood exceeds one window
+            const long long s_abs = v.s_abs;
+            int tt = 0;
+            const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), v.hx, v.hy, v.hz, lane, tt);
+            build_window(B, (int)(s_abs & 1), c, w * kListAtoms, lane, wa);
+            if (lane == 0) wa.built = w;
+            __syncwarp();
+        }
+        if (act) {
+            if (w == 0) {   // the home atoms sit at the front of window 0
+                const int a0 = ib + 2 * pi, a1 = ib + min(2 * pi + 1, nin - 1);   // odd nin: repeat an atom
+                const float4 q0 = wa.list[a0], q1 = wa.list[a1];
+                X = make_float2(q0.x, q1.x);
+                Y = make_float2(q0.y, q1.y);
+                Z = make_float2(q0.z, q1.z);
+            }
+            const unsigned rcb = __float_as_uint(B.rc2f);
+            const float rc2f = B.rc2f, ush = B.ushiftf;
+            const int wn = min(kListAtoms, total - w * kListAtoms);
+            const int hn = w == 0 ? n_home : 0;
+            for (int t = g; t < hn; t += ns) pair2<true, OBS>(X, Y, Z, wa.list[t], rc2f, rcb, ush, acc);
+            const int M = wn - hn;
+            const int chunk = qdiv(M + ns - 1, inv_of(ns));
+            const float4 *lp = wa.list + hn + g * chunk;
+            const float4 *le = wa.list + hn + min(M, g * chunk + chunk);
+DSEA_UNROLL(DSEA_PAIR_UNROLL_N)
+            for (; lp < le; ++lp) pair2<OBS, OBS>(X, Y, Z, *lp, rc2f, rcb, ush, acc);
+        }
+    }
+    // combine the ns partials of each atom pair into lane pi, in group order
+    const float2 FX = acc.fx, FY = acc.fy, FZ = acc.fz, UU = acc.u, WW = acc.w;
+    float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
+    for (int gg = 1; gg < ns; ++gg) {
+        const int src = pi + gg * np;   // < ns * np <= 32
+        SX.x += __shfl_sync(kFull, FX.x, src); SX.y += __shfl_sync(kFull, FX.y, src);
+        SY.x += __shfl_sync(kFull, FY.x, src); SY.y += __shfl_sync(kFull, FY.y, src);
+        SZ.x += __shfl_sync(kFull, FZ.x, src); SZ.y += __shfl_sync(kFull, FZ.y, src);
+        if (OBS) {
+            SU.x += __shfl_sync(kFull, UU.x, src); SU.y += __shfl_sync(kFull, UU.y, src);
+            SW.x += __shfl_sync(kFull, WW.x, src); SW.y += __shfl_sync(kFull, WW.y, src);
+        }
+    }
+    // atom l (l < nin) is half l & 1 of the pair held by lane l >> 1
+    const int from = (lane >> 1) < np ? (lane >> 1) : 0;
+    const bool hi = lane & 1;
+    float t0, t1;
+    t0 = __shfl_sync(kFull, SX.x, from); t1 = __shfl_sync(kFull, SX.y, from); fx = hi ? t1 : t0;
+    t0 = __shfl_sync(kFull, SY.x, from); t1 = __shfl_sync(kFull, SY.y, from); fy = hi ? t1 : t0;
+    t0 = __shfl_sync(kFull, SZ.x, from); t1 = __shfl_sync(kFull, SZ.y, from); fz = hi ? t1 : t0;
+    if (OBS) {
+        t0 = __shfl_sync(kFull, SU.x, from); t1 = __shfl_sync(kFull, SU.y, from); uu = hi ? t1 : t0;
+        t0 = __shfl_sync(kFull, SW.x, from); t1 = __shfl_sync(kFull, SW.y, from); ww = hi ? t1 : t0;
+    }
+}
+
+// Kick, drift and rebin (INTEGRATE) or read back (OBS without INTEGRATE) the
+// home atoms [ib, ib + 32) of the warp's home cell, given their forces;
+// OBS adds their U, W and KE halves to red_*.
+template <bool INTEGRATE, bool OBS>
+__device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int ib, int lane, float fx, float fy,
+                                            float fz, float uu, float ww, double &red_u, double &red_w,
+                                            double &red_k)
+{
+    const volatile WarpArea &v = wa;
+    const long long s_abs = v.s_abs;
+    const int p = (int)(s_abs & 1), pn = p ^ 1;
+    const unsigned tag_next = (unsigned)(s_abs + 2);
+    const bool first_step = v.first != 0;
+    const long long S = B.n_slots;
+    const float dtf = (float)B.dt;
+    const int n_home = v.n_home;
+    const bool own = lane < n_home - ib;
+    long long slot = 0;
+    int aid = 0;
+    float4 qo = make_float4(0.f, 0.f, 0.f, 0.f);
+    double rr[3] = {0.0, 0.0, 0.0};
+    float vv[3] = {0.f, 0.f, 0.f};
+    if (own) {
+        slot = wa.hslot[ib + lane];
+        qo = v.total <= kListAtoms ? wa.list[ib + lane] : __ldcg(B.q[p] + slot);
+        aid = __float_as_int(qo.w);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            rr[d] = __ldcg(B.r[p] + d * S + slot);
+            vv[d] = __ldcg(B.vf[p] + d * S + slot);
+        }
+        if (OBS) {
+            // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
+            const float hk = first_step ? 0.f : 0.5f * dtf;
+            const float sx = fmaf(hk, fx, vv[0]), sy = fmaf(hk, fy, vv[1]), sz = fmaf(hk, fz, vv[2]);
+            red_u += 0.5 * (double)uu;
+            red_w += 0.5 * (double)ww;
+            red_k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+            if (!INTEGRATE) {
+                const long long o = 3LL * aid;
+                B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
+                B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
+                B.out_r[o] = rr[0]; B.out_r[o + 1] = rr[1]; B.out_r[o + 2] = rr[2];
+            }
+        }
+    }
+    if (INTEGRATE) {
+        long long dest = 0;
+        float qn[3] = {0.f, 0.f, 0.f};
+        if (own) {
+            const float kf = first_step ? 0.5f * dtf : dtf;
+            vv[0] = fmaf(kf, fx, vv[0]);   // v(t + dt/2) = v(t - dt/2) + F dt
+            vv[1] = fmaf(kf, fy, vv[1]);
+            vv[2] = fmaf(kf, fz, vv[2]);
+            const float q3[3] = {qo.x, qo.y, qo.z};
+            const int cg[3] = {v.hx, v.hy, v.hz};
+            int c3[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
+                c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], wa.ctab + 3 * d, B.lc[d], B.inv_lcf[d],
+                                  B.L[d], B.nc[d], qn[d]);
+            const int dj = qdiv(c3[0], inv_of(B.cps)) - v.j;
+            const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
+            if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
+            dest = ((long long)c3[0] * B.nc[1] + c3[1]) * B.nc[2] + c3[2];
+        }
+        int n_stay = v.n_stay;
+        const long long slot_n = place_slot(B, pn, v.hcell, dest, own, tag_next, lane, n_stay);
+        if (slot_n >= 0)
+            store_mixed(B, pn, slot_n, aid, rr[0], rr[1], rr[2], vv[0], vv[1], vv[2], qn[0], qn[1], qn[2]);
+        __syncwarp();
+        if (lane == 0) wa.n_stay = n_stay;
+    }
+}
+
+// One home cell (wa.hx, wa.hy, wa.hz) of the mixed form, warp-wide: its
+// neighbourhood into the list, forces, then home_update per 32 home atoms;
+// INTEGRATE publishes how many atoms stayed in the cell.
+template <bool INTEGRATE, bool OBS>
+__device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, double &red_u, double &red_w,
+                                                double &red_k)
+{
+    const int lane = threadIdx.x & 31;
+    const volatile WarpArea &v = wa;
+    {
+        const long long s_abs = v.s_abs;
+        const int hx = v.hx, hy = v.hy, hz = v.hz;
+        int total = 0;
+        const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), hx, hy, hz, lane, total);
+        build_window(B, (int)(s_abs & 1), c, 0, lane, wa);
+        if (lane == 0) {
+            wa.n_home = c.n_s + c.n_a;
+            wa.hcell = c.gc;
+            wa.total = total;
+            wa.built = 0;
+            wa.n_stay = 0;
+        }
+        if (lane < 9) {
+            const int ax = lane / 3, o = lane - 3 * (lane / 3) - 1;
+            const int cg = ax == 0 ? hx : (ax == 1 ? hy : hz);
+            wa.ctab[lane] = ((double)(cg + o) + 0.5) * B.lc[ax];
+        }
+        __syncwarp();
+    }
+    for (int ib = 0; ib < v.n_home; ib += 32) {
+        float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
+        home_forces<OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww);
+        home_update<INTEGRATE, OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww, red_u, red_w, red_k);
+    }
+    // the home cell publishes how many atoms stayed in it, empty or not
+    if (INTEGRATE && lane == 0)
+        B.cnt[(int)(v.s_abs & 1) ^ 1][v.hcell] = ((unsigned long long)(unsigned)(v.s_abs + 2) << 32) |
+                                                  (unsigned long long)(unsigned)v.n_stay;
+    __syncwarp();   // the list and slot table are reused by the next home cell
+}
+
+// Home cell h of unit (j, tile) (z fastest, then y, then x) into wa.hx/hy/hz.
+__device__ __forceinline__ int unit_cell_count(const BoxDev &B, int tile)
+{
+    const int tyi = qdiv(tile, inv_of(B.tiles_z)), tzi = tile - tyi * B.tiles_z;
+    return B.cps * min(B.tile_y, B.nc[1] - tyi * B.tile_y) * min(B.tile_z, B.nc[2] - tzi * B.tile_z);
+}
+__device__ __forceinline__ void set_unit_cell(const BoxDev &B, WarpArea &wa, int j, int tile, int h)
+{
+    const int tyi = qdiv(tile, inv_of(B.tiles_z)), tzi = tile - tyi * B.tiles_z;
+    const int y0 = tyi * B.tile_y, z0 = tzi * B.tile_z;
+    const int ny = min(B.tile_y, B.nc[1] - y0), nz = min(B.tile_z, B.nc[2] - z0);
+    const int nyz = ny * nz;
+    const int lx = qdiv(h, inv_of(nyz)), r = h - lx * nyz, ly = qdiv(r, inv_of(nz));
+    if ((threadIdx.x & 31) == 0) {
+        wa.hx = j * B.cps + lx;
+        wa.hy = y0 + ly;
+        wa.hz = z0 + (r - ly * nz);
+    }
+    __syncwarp();
 }
 
 // ---- kernels ---------------------------------------------------------------
@@ -962,8 +1050,9 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
     }
 }
 
-template <int PREC, bool INTEGRATE, bool OBS>
-__global__ void __launch_bounds__(kThreads) k_units(const BoxDev *bp, long long s_abs, int first)
+// FP64 form, one step or force pass: one CTA per unit.
+template <bool INTEGRATE, bool OBS>
+__global__ void __launch_bounds__(kThreads) k_units_f64(const BoxDev *bp, long long s_abs, int first)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;
@@ -971,7 +1060,46 @@ __global__ void __launch_bounds__(kThreads) k_units(const BoxDev *bp, long long 
     __syncthreads();
     const int u = blockIdx.x;
     const int j = u / sB.units_per_slice, tile = u - j * sB.units_per_slice;
-    run_unit<PREC, INTEGRATE, OBS>(sB, j, tile, s_abs, first != 0, u, smem);
+    run_unit_f64<INTEGRATE, OBS>(sB, j, tile, s_abs, first != 0, u, smem);
+}
+
+// Mixed form, one step or force pass: one warp per unit (warp w of block b
+// takes unit b * kWarps + w); the unit's home cells in order.
+template <bool INTEGRATE, bool OBS>
+__global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long long s_abs, int first)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ BoxDev sB;
+    if (threadIdx.x == 0) sB = *bp;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int u = blockIdx.x * kWarps + warp;
+    if (u >= sB.n_slices * sB.units_per_slice) return;
+    WarpArea &wa = reinterpret_cast<WarpArea *>(smem)[warp];
+    const int j = u / sB.units_per_slice, tile = u - j * sB.units_per_slice;
+    if (lane == 0) {
+        wa.s_abs = s_abs;
+        wa.j = j;
+        wa.first = first;
+    }
+    double red_u = 0.0, red_w = 0.0, red_k = 0.0;
+    const int n = unit_cell_count(sB, tile);
+    for (int h = 0; h < n; ++h) {
+        set_unit_cell(sB, wa, j, tile, h);
+        mixed_home_cell<INTEGRATE, OBS>(sB, wa, red_u, red_w, red_k);
+    }
+    if (OBS) {   // fixed-order FP64 reduction of the unit: xor tree over the lanes
+        for (int o = 16; o > 0; o >>= 1) {
+            red_u += __shfl_xor_sync(kFull, red_u, o);
+            red_w += __shfl_xor_sync(kFull, red_w, o);
+            red_k += __shfl_xor_sync(kFull, red_k, o);
+        }
+        if (lane == 0) {
+            sB.unit_obs[3LL * u] = red_u;
+            sB.unit_obs[3LL * u + 1] = red_w;
+            sB.unit_obs[3LL * u + 2] = red_k;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int n, double *out3)
@@ -1002,19 +1130,18 @@ __global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int 
     }
 }
 
-// The persistent ring: every CTA is one on-chip stage that repeatedly takes
-// the next ticket, waits (bounded) until the five slices its unit reads at
-// the previous level are complete, runs the unit and reports completion.
-// Tickets are dispensed step-major and, within a step, slice by slice from
-// an offset that advances two slices per step, so level s trails level s-1
-// by about five slices (the time-skewed cyclic order of Sec. 3.1 / Table 1).
-// A CTA only waits on tickets smaller than its own, all of which were taken
-// by running CTAs, so the ring always progresses.
+// The persistent ring of the FP64 form: every CTA is one on-chip stage that
+// repeatedly takes the next ticket, waits (bounded) until the five slices
+// its unit reads at the previous level are complete, runs the unit and
+// reports completion.  Tickets are dispensed step-major and, within a step,
+// slice by slice from an offset that advances two slices per step, so level
+// s trails level s-1 by about five slices (the time-skewed cyclic order of
+// Sec. 3.1 / Table 1).  A CTA only waits on tickets smaller than its own, all
+// of which were taken by running CTAs, so the ring always progresses.
 #ifndef DSEA_RING_MIN_BLOCKS
 #define DSEA_RING_MIN_BLOCKS 4   // CTAs per SM the register allocation must allow
 #endif
-template <int PREC>
-__global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring(RingPlan plan)
+__global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(RingPlan plan)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;
@@ -1089,10 +1216,112 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring(RingPla
         const int s_rel = s_dec[0], j = s_dec[1], tile = s_dec[2];
         const long long s_abs = sB.step + s_rel;
         if (s_go == 1)
-            run_unit<PREC, true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
+            run_unit_f64<true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
         __threadfence();
         __syncthreads();
         if (tid == 0 && !(j == sB.withhold_slice && s_rel == 0)) atomicAdd(sB.done + j, 1u);
+    }
+}
+
+// The persistent ring of the mixed form: every warp is one stage.  Lane 0
+// takes the next ticket, the warp loads the ticket's box descriptor into its
+// own shared memory if it changed, lane 0 waits (bounded) until slices
+// j-2..j+2 of the previous level are complete, the warp runs the unit's home
+// cells and reports completion.  Same dispatch order, dependency rule and
+// failure handling as the CTA-level ring; a warp only waits on tickets
+// smaller than its own, all taken by running warps.
+__global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(RingPlan plan)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ BoxDev s_box[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpArea &wa = reinterpret_cast<WarpArea *>(smem)[warp];
+    const volatile WarpArea &v = wa;
+    BoxDev &B = s_box[warp];
+    double red_u = 0.0, red_w = 0.0, red_k = 0.0;   // unused (no reduction in the ring)
+    if (lane == 0) wa.box = -1;
+    __syncwarp();
+    while (true) {
+        int go = 1;   // 0: stop the warp, 1: run the unit, 2: skip it
+        int bl = 0;
+        long long r = 0;
+        if (lane == 0) {
+            const long long t = (long long)atomicAdd(plan.ticket, 1ULL);
+            if (t >= plan.total) {
+                go = 0;
+            } else {
+                int lo = 0, hi = plan.n_steps - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (plan.step_base[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                wa.rel = lo;
+                r = t - plan.step_base[lo];
+                int bh = plan.active[lo] - 1;
+                while (bl < bh) {
+                    const int mid = (bl + bh + 1) >> 1;
+                    if (plan.cum_units[mid] <= r) bl = mid; else bh = mid - 1;
+                }
+            }
+        }
+        go = __shfl_sync(kFull, go, 0);
+        if (go == 0) break;
+        bl = __shfl_sync(kFull, bl, 0);
+        if (bl != v.box) {   // the warp's copy of the box descriptor
+            const int *src = reinterpret_cast<const int *>(plan.boxes + bl);
+            int *dst = reinterpret_cast<int *>(&B);
+            for (int i = lane; i < (int)(sizeof(BoxDev) / sizeof(int)); i += 32) dst[i] = src[i];
+            __syncwarp();
+            if (lane == 0) wa.box = bl;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int s_rel = wa.rel;
+            const int m = (int)(r - plan.cum_units[bl]);
+            const int ups = B.units_per_slice;
+            const int jj = m / ups;
+            const int j = ring_slice(jj, B.step + s_rel, B.n_slices);
+            wa.j = j;
+            wa.tile = m - jj * ups;
+            wa.s_abs = B.step + s_rel;
+            wa.first = (s_rel == 0 && B.w_is_sync) ? 1 : 0;
+            if (ld_volatile_int(plan.err) != 0) go = 0;
+            else if (ld_volatile_int(B.err) != 0) go = 2;
+            if (go == 1 && s_rel > 0) {
+                const unsigned need = (unsigned)ups * (unsigned)s_rel;
+                const unsigned long long t0 = global_ns();
+                for (int d = -2; d <= 2 && go == 1; ++d) {
+                    const int k = wrap_index(j + d, B.n_slices);
+                    unsigned sleep = 32;
+                    while (ld_acquire(B.done + k) < need) {
+                        if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
+                        if ((long long)(global_ns() - t0) > B.wait_limit_ns) {
+                            atomicCAS(plan.err, 0, kErrTimeout);
+                            for (int q = 0; q < plan.n_boxes; ++q) set_error(plan.boxes[q].err, kErrTimeout);
+                            go = 0;
+                            break;
+                        }
+                        __nanosleep(sleep);
+                        if (sleep < 1024) sleep <<= 1;
+                    }
+                }
+            }
+        }
+        go = __shfl_sync(kFull, go, 0);
+        if (go == 0) break;
+        if (go == 1) {
+            const int n = unit_cell_count(B, v.tile);
+            for (int h = 0; h < n; ++h) {
+                set_unit_cell(B, wa, v.j, v.tile, h);
+                mixed_home_cell<true, false>(B, wa, red_u, red_w, red_k);
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            const int j = v.j;
+            if (!(j == B.withhold_slice && v.rel == 0)) atomicAdd(B.done + j, 1u);
+        }
     }
 }
 
@@ -1106,7 +1335,8 @@ cudaError_t set_smem(K kernel, size_t bytes)
 
 size_t unit_smem_bytes(int precision, int staged_cells, int smem_atoms)
 {
-    return make_layout(precision, staged_cells, smem_atoms).total;
+    if (precision == 1) return sizeof(WarpArea) * kWarps;   // per-warp lists, whatever the unit
+    return make_layout(staged_cells, smem_atoms).total;
 }
 
 size_t max_unit_smem_bytes()
@@ -1134,10 +1364,17 @@ static cudaError_t launch_units(const BoxDev &hb, const BoxDev *db, long long s_
                                 cudaStream_t stream)
 {
     const size_t smem = unit_smem_bytes(PREC, hb.staged_cells, hb.smem_atoms);
-    cudaError_t e = set_smem(k_units<PREC, INTEGRATE, OBS>, smem);
+    const int units = hb.n_slices * hb.units_per_slice;
+    if (PREC == 1) {
+        cudaError_t e = set_smem(k_units_mixed<INTEGRATE, OBS>, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = (units + kWarps - 1) / kWarps;
+        k_units_mixed<INTEGRATE, OBS><<<grid, kThreads, smem, stream>>>(db, s_abs, first);
+        return cudaGetLastError();
+    }
+    cudaError_t e = set_smem(k_units_f64<INTEGRATE, OBS>, smem);
     if (e != cudaSuccess) return e;
-    const int grid = hb.n_slices * hb.units_per_slice;
-    k_units<PREC, INTEGRATE, OBS><<<grid, kThreads, smem, stream>>>(db, s_abs, first);
+    k_units_f64<INTEGRATE, OBS><<<units, kThreads, smem, stream>>>(db, s_abs, first);
     return cudaGetLastError();
 }
 
@@ -1166,13 +1403,13 @@ cudaError_t launch_ring(const RingPlan &plan, int precision, size_t smem_bytes, 
     if (plan.total == 0) return cudaSuccess;
     cudaError_t e;
     if (precision == 1) {
-        e = set_smem(k_ring<1>, smem_bytes);
+        e = set_smem(k_ring_mixed, smem_bytes);
         if (e != cudaSuccess) return e;
-        k_ring<1><<<ctas, kThreads, smem_bytes, stream>>>(plan);
+        k_ring_mixed<<<ctas, kThreads, smem_bytes, stream>>>(plan);
     } else {
-        e = set_smem(k_ring<0>, smem_bytes);
+        e = set_smem(k_ring_f64, smem_bytes);
         if (e != cudaSuccess) return e;
-        k_ring<0><<<ctas, kThreads, smem_bytes, stream>>>(plan);
+        k_ring_f64<<<ctas, kThreads, smem_bytes, stream>>>(plan);
     }
     return cudaGetLastError();
 }
@@ -1181,11 +1418,11 @@ int ring_ctas_per_sm(int precision, size_t smem_bytes)
 {
     int n = 0;
     if (precision == 1) {
-        set_smem(k_ring<1>, smem_bytes);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring<1>, kThreads, smem_bytes);
+        set_smem(k_ring_mixed, smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring_mixed, kThreads, smem_bytes);
     } else {
-        set_smem(k_ring<0>, smem_bytes);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring<0>, kThreads, smem_bytes);
+        set_smem(k_ring_f64, smem_bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ring_f64, kThreads, smem_bytes);
     }
     return n;
 }
