@@ -421,19 +421,20 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
         // stayer and arrival counts of every cell, one allocation
         hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * 2 * hb.n_cells);
         hb.arr[q] = hb.cnt[q] ? hb.cnt[q] + hb.n_cells : nullptr;
-        hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
         hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        hb.id[q] = nullptr;
         hb.v[q] = nullptr;
         hb.vf[q] = nullptr;
         hb.q[q] = nullptr;
-        if (p.precision == DSEA_MIXED) {
+        if (p.precision == DSEA_MIXED) {   // the atom id travels in q.w
             hb.vf[q] = (float *)dev_alloc(b, sizeof(float) * 3 * hb.n_slots);
             hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
         } else {
+            hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
             hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
         }
-        if (!hb.cnt[q] || !hb.id[q] || !hb.r[q] ||
-            (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : !hb.v[q]))
+        if (!hb.cnt[q] || !hb.r[q] ||
+            (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : (!hb.v[q] || !hb.id[q])))
             return DSEA_ERR_OOM;
         CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * 2 * hb.n_cells, b->stream));
     }
@@ -699,11 +700,13 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         const bool mixed = hb.precision == DSEA_MIXED;
         const size_t b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
         void *s_cnt = nullptr, *s_id = nullptr, *s_r = nullptr, *s_v = nullptr, *s_q = nullptr;
-        bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess && cudaMalloc(&s_id, b_id) == cudaSuccess &&
+        bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess &&
+                  (mixed || cudaMalloc(&s_id, b_id) == cudaSuccess) &&
                   cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_v) == cudaSuccess &&
-                  (hb.precision != DSEA_MIXED || cudaMalloc(&s_q, b_q) == cudaSuccess);
+                  (!mixed || cudaMalloc(&s_q, b_q) == cudaSuccess);
         auto release = [&]() {
-            cudaFree(s_cnt); cudaFree(s_id); cudaFree(s_r); cudaFree(s_v);
+            cudaFree(s_cnt); cudaFree(s_r); cudaFree(s_v);
+            if (s_id) cudaFree(s_id);
             if (s_q) cudaFree(s_q);
         };
         if (!ok) {
@@ -717,7 +720,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
                             : cudaMemcpyAsync(live, snap, bytes, cudaMemcpyDeviceToDevice, b->stream);
             };
             cudaError_t e = c(s_cnt, hb.cnt[p], b_cnt);
-            if (e == cudaSuccess) e = c(s_id, hb.id[p], b_id);
+            if (e == cudaSuccess && s_id) e = c(s_id, hb.id[p], b_id);
             if (e == cudaSuccess) e = c(s_r, hb.r[p], b_r);
             if (e == cudaSuccess) e = c(s_v, mixed ? (void *)hb.vf[p] : (void *)hb.v[p], b_v);
             if (e == cudaSuccess && s_q) e = c(s_q, hb.q[p], b_q);
@@ -931,8 +934,8 @@ int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, siz
     double mean_cap = 0;
     int rc = setup_geometry(desc->n_slices, desc->box, desc->n_atoms, p, hb, mean_cap);
     if (rc) return rc;
-    const size_t per_slot = sizeof(int) + 3 * sizeof(double) +
-                            (p.precision == DSEA_MIXED ? 3 * sizeof(float) + sizeof(float4) : 3 * sizeof(double));
+    const size_t per_slot = 3 * sizeof(double) + (p.precision == DSEA_MIXED ? 3 * sizeof(float) + sizeof(float4)
+                                                                            : sizeof(int) + 3 * sizeof(double));
     size_t b = 2 * ((size_t)hb.n_cells * 2 * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
     b += (size_t)hb.n_cells * 3 * sizeof(double);              // unit partials
     b += (size_t)desc->n_atoms * 9 * sizeof(double);           // read-back arrays

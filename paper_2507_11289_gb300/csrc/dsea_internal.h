@@ -52,8 +52,8 @@ struct BoxDev {
     // state, two step-parity buffers
     unsigned long long *cnt[2];  // per cell: (tag << 32) | stayers, tag = step + 1
     unsigned long long *arr[2];  // per cell: (tag << 32) | arrivals
-    int *id[2];
-    double *r[2];   // absolute positions, 3 * n_slots
+    int *id[2];     // FP64 form: atom ids (the mixed form keeps them in q.w)
+    double *r[2];   // FP64 form: absolute positions; mixed: relative to the atom's cell centre
     double *v[2];   // FP64 form: velocities (half-step after the first step), 3 * n_slots
     float *vf[2];   // mixed form: the same velocities in FP32, 3 * n_slots
     float4 *q[2];   // mixed: cell-centred FP32 coordinates, atom id bits in .w

@@ -60,6 +60,19 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// Asynchronous 16-byte global -> shared copy that bypasses L1 (.cg), so data
+// other SMs wrote earlier in the same persistent launch is always seen (L1 is
+// not kept coherent with other SMs' writes).  Both addresses 16-B aligned.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // floor(a / d) for 0 <= a < 2^22 through the FP32 reciprocal inv_d = 1/d
@@ -167,18 +180,20 @@ struct Acc2 {
     float2 fx, fy, fz, u, w;
 };
 
-// Two home atoms (XS, YS, ZS: already in the neighbour cell's frame) against
-// one staged neighbour.  EXACT: the cutoff test also excludes r2 == 0 (the
-// atom itself; needed in the home cell) and masks the energy terms; otherwise
-// the force is masked by multiplying with the 0/1 cutoff mask, which gives
-// the same bits for every pair of distinct atoms.
+// Two candidate pairs at once in packed FP32x2: half 0 of (XS, YS, ZS) against
+// half 0 of (XJ, YJ, ZJ), half 1 against half 1.  EXACT: the cutoff test
+// also excludes r2 == 0 (an atom against itself; needed in the home cell)
+// and masks the energy terms; otherwise the force is masked by multiplying
+// with the 0/1 cutoff mask, which gives the same bits for every pair of
+// distinct atoms.
 template <bool EXACT, bool OBS>
-__device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const float2 ZS, const float4 pj,
-                                      float rc2f, unsigned rcb, float ushiftf, Acc2 &a)
+__device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const float2 ZS, const float2 XJ,
+                                      const float2 YJ, const float2 ZJ, float rc2f, unsigned rcb, float ushiftf,
+                                      Acc2 &a)
 {
-    const float2 DX = f2sub(XS, f2splat(pj.x));
-    const float2 DY = f2sub(YS, f2splat(pj.y));
-    const float2 DZ = f2sub(ZS, f2splat(pj.z));
+    const float2 DX = f2sub(XS, XJ);
+    const float2 DY = f2sub(YS, YJ);
+    const float2 DZ = f2sub(ZS, ZJ);
     const float2 R2 = f2fma(DZ, DZ, f2fma(DY, DY, f2mul(DX, DX)));
     const float2 R2I = make_float2(rcp_approx(R2.x), rcp_approx(R2.y));
     const float2 A = f2mul(R2I, R2I);
@@ -302,14 +317,14 @@ __device__ __forceinline__ void store_f64(const BoxDev &B, int pn, long long slo
     B.v[pn][2 * S + slot] = vz;
 }
 
-// Write one atom into slot `slot` of buffer `pn` (mixed form): FP64 absolute
-// position, FP32 velocity, FP32 coordinates relative to its cell centre.
+// Write one atom into slot `slot` of buffer `pn` (mixed form): FP64 position
+// relative to its cell centre, FP32 velocity, FP32 copy of the position with
+// the atom id in .w.
 __device__ __forceinline__ void store_mixed(const BoxDev &B, int pn, long long slot, int aid, double x,
                                             double y, double z, float vx, float vy, float vz, float qx,
                                             float qy, float qz)
 {
     const long long S = B.n_slots;
-    B.id[pn][slot] = aid;
     B.r[pn][slot] = x;
     B.r[pn][S + slot] = y;
     B.r[pn][2 * S + slot] = z;
@@ -334,29 +349,22 @@ __device__ __forceinline__ int cell_of(double x, double inv_lc, int n)
     return c < 0 ? 0 : (c >= n ? n - 1 : c);
 }
 
-// Destination of a mixed-form atom along one axis.  The atom sat in home cell
-// `cg` with FP32 coordinate q relative to its centre and moved by d (FP32).
-// Returns the unwrapped destination cell and sets the new FP32 coordinate
-// relative to that cell's centre (from the FP64 position) and the wrapped
-// FP64 position.  ctab3 holds the FP64 centres of cells cg-1, cg, cg+1.
-__device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, const double *ctab3,
-                                         double lc, float inv_lcf, double L, int nc, float &qn)
+// Destination of a mixed-form atom along one axis.  The atom sat in cell cg
+// at FP64 position r relative to that cell's centre (FP32 copy q) and moves
+// by d (FP32).  The cell offset is decided in FP32; r becomes the FP64
+// position relative to the destination cell's centre and qn its FP32 copy.
+// Returns the destination cell, wrapped periodically (a relative position
+// needs no wrap).  Three FP64 operations in the common case.
+__device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, double lc, float inv_lcf, int nc,
+                                         float &qn)
 {
     const int o = (int)floorf(fmaf(q + d, inv_lcf, 0.5f));   // cell offset, usually -1, 0 or 1
-    const int cu = cg + o;
-    const double ru = r + (double)d;                         // FP64 position update (unwrapped)
-    const double cen = (o >= -1 && o <= 1) ? ctab3[o + 1] : ((double)cu + 0.5) * lc;
-    qn = (float)(ru - cen);
-    int c = cu;
-    double rw = ru;
-    if (c < 0) {
-        c += nc;
-        rw += L;
-    } else if (c >= nc) {
-        c -= nc;
-        rw -= L;
-    }
-    r = rw;
+    double rn = r + (double)d;                               // FP64 position update
+    if (o != 0) rn -= (double)o * lc;                        // rebase on the new cell's centre
+    r = rn;
+    qn = (float)rn;
+    int c = cg + o;
+    c = c < 0 ? c + nc : (c >= nc ? c - nc : c);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
@@ -671,38 +679,54 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
 // FP32 coordinates shifted into the home cell's centred frame (home cell
 // first, then the 26 others in (ox, oy, oz) order), and evaluates its home
 // atoms against that list with packed FP32x2 arithmetic, then kicks, drifts
-// and rebins them.  A neighbourhood longer than the list is processed in
-// windows of kListAtoms.  There is no unit-wide staging, so warps never wait
-// for each other inside a unit.
+// and rebins them.  The list stores entries in pairs, [x0 x1 y0 y1 | z0 z1 -
+// -], so that one pair of neighbours loads straight into the halves of packed
+// operands; each lane holds two home atoms as splatted operands and meets two
+// neighbours per loop trip (four candidate pairs).  The home cell's segment
+// and the whole list are padded to an even length with a far-away dummy.  A
+// neighbourhood longer than the list is processed in windows of kListAtoms.
+// There is no unit-wide staging, so warps never wait for each other.
 
-constexpr int kListAtoms = 352;   // list window (atoms) of one warp
-constexpr int kHomeMax = 128;     // largest cell capacity (slots of one home cell)
+#ifndef DSEA_LIST_ATOMS
+#define DSEA_LIST_ATOMS 352
+#endif
+constexpr int kListAtoms = DSEA_LIST_ATOMS;   // list window (entries, even) of one warp
+constexpr int kHomeMax = 128;                 // largest cell capacity (slots of one home cell)
+constexpr float kFarAway = 1.0e4f;            // coordinate of a padding entry (never within the cutoff)
 
 // Per-warp shared memory of the mixed form.  The context fields are written
 // once per home cell and read back through volatile loads where they are
 // needed, so that no register holds them across the pair loop.
 struct WarpArea {
-    float4 list[kListAtoms];   // neighbour window: x, y, z in the home frame, atom id bits
+    float4 list[kListAtoms];   // kListAtoms / 2 entry pairs: [x0 x1 y0 y1], [z0 z1 id0 id1]
     int hslot[kHomeMax];       // slot of each home atom, in the cell's canonical order
-    double ctab[9];            // FP64 centres of home cells cg-1, cg, cg+1 per axis
     long long s_abs;           // step of the input state
     long long hcell;           // home cell
     int j, tile, first;        // unit and first-step flag
     int rel, box;              // ring: relative step and box of the unit
     int hx, hy, hz;            // home cell coordinates
-    int n_home, total, built;  // home atoms, neighbourhood atoms, window held by the list
+    int n_home, total, built;  // home atoms, list length (padded), window held by the list
     int n_stay;                // atoms that stayed in the home cell so far
 };
+
+// Entry e of the list window: its x (y, z and the id bits follow at +2,
+// +4 and +6 floats).
+__device__ __forceinline__ float *list_entry(WarpArea &wa, int e)
+{
+    return reinterpret_cast<float *>(&wa.list[2 * (e >> 1)]) + (e & 1);
+}
 
 // Lane c (< 27) of a warp describes one cell of the neighbourhood of home
 // cell (hx, hy, hz): lane 0 the home cell, lanes 1..26 the others.
 struct NbrCell {
     int gc;           // global cell index
     int n_s, n_a;     // stayers (front slots) and arrivals (back slots)
-    int pre;          // first list position of the cell
+    int pre;          // first list entry of the cell
     float sx, sy, sz; // shift of the cell's centre from the home cell's centre
 };
 
+// The neighbourhood of a home cell; `total` receives the list length, padded
+// to even (the home segment is padded to even as well).
 __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag, int hx, int hy, int hz,
                                             int lane, int &total)
 {
@@ -729,35 +753,39 @@ __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag
         c.sz = (float)oz * B.lcf[2];
     }
     const int n = c.n_s + c.n_a;
-    int incl = n;
+    const int nl = lane == 0 ? (n + 1) & ~1 : n;   // the home segment ends on a pair boundary
+    int incl = nl;
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += v;
     }
-    c.pre = incl - n;
-    total = __shfl_sync(kFull, incl, 31);
+    c.pre = incl - nl;
+    const int t = __shfl_sync(kFull, incl, 31);
+    total = (t + 1) & ~1;
     return c;
 }
 
-// Copy list positions [w0, w0 + kListAtoms) of the neighbourhood into the
+// Copy list entries [w0, w0 + kListAtoms) of the neighbourhood into the
 // warp's list (lane c copies its cell's share).  A cell's canonical order is
 // its stayers in slot order, then its arrivals ordered by atom id.  Home
-// cell entries also record their slot.
-__device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCell &c, int w0, int lane,
-                                             WarpArea &wa)
+// cell entries also record their slot.  Padding entries sit far away.  The
+// stayers arrive by asynchronous 16-byte copies (all of a cell's in flight at
+// once) as whole entries; each lane then shifts its cell's entries into the
+// home frame, and one warp-wide pass turns every two entries into the
+// [x0 x1 y0 y1 | z0 z1 w0 w1] pair layout in place.
+__device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCell &c, int total, int w0,
+                                             int lane, WarpArea &wa)
 {
+    const int w1 = w0 + kListAtoms;
+    float4 *raw = wa.list;   // entry e of the window at raw[e] until the pair pass
     if (lane < 27) {
         const float4 *q = B.q[p];
-        const int w1 = w0 + kListAtoms;
         const long long base = (long long)c.gc * B.cap;
         // stayers: canonical position i = slot offset i
         const int lo = max(0, w0 - c.pre), hi = min(c.n_s, w1 - c.pre);
-#pragma unroll 2
         for (int i = lo; i < hi; ++i) {
-            const long long slot = base + i;
-            const float4 a = __ldcg(q + slot);
-            wa.list[c.pre + i - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
-            if (lane == 0) wa.hslot[i] = (int)slot;
+            cp_async16(&raw[c.pre + i - w0], q + base + i);
+            if (lane == 0) wa.hslot[i] = (int)(base + i);
         }
         // arrivals: slot cap-1-k holds the k-th arrival; order them by id
         const long long abase = base + B.cap - c.n_a;
@@ -774,21 +802,43 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
             }
             const int cp = a0 + r;   // canonical list position
             if (cp >= w0 && cp < w1) {
-                wa.list[cp - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
+                raw[cp - w0] = a;
                 if (lane == 0) wa.hslot[c.n_s + r] = (int)slot;
             }
         }
+        // padding: after an odd home cell, and after an odd list
+        const int pad0 = c.n_s + c.n_a;   // lane 0: the home cell's count
+        if (lane == 0 && (pad0 & 1) && pad0 >= w0 && pad0 < w1)
+            raw[pad0 - w0] = make_float4(kFarAway, kFarAway, kFarAway, 0.f);
+        if (lane == 26 && c.pre + c.n_s + c.n_a < total && total - 1 >= w0 && total - 1 < w1)
+            raw[total - 1 - w0] = make_float4(kFarAway, kFarAway, kFarAway, 0.f);
+        cp_async_wait_all();
+        if (lane > 0) {   // into the home cell's frame
+            const int e0 = max(c.pre, w0), e1 = min(c.pre + c.n_s + c.n_a, w1);
+            for (int e = e0; e < e1; ++e) {
+                const float4 a = raw[e - w0];
+                raw[e - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
+            }
+        }
+    }
+    __syncwarp();
+    const int n_pairs = min(kListAtoms, total - w0) >> 1;
+    for (int b = lane; b < n_pairs; b += 32) {
+        const float4 e0 = raw[2 * b], e1 = raw[2 * b + 1];
+        raw[2 * b] = make_float4(e0.x, e1.x, e0.y, e1.y);
+        raw[2 * b + 1] = make_float4(e0.z, e1.z, e0.w, e1.w);
     }
     __syncwarp();
 }
 
 // Forces on home atoms [ib, ib + nin) of the warp's home cell from the whole
 // neighbourhood (all windows), packed FP32x2: each lane carries two home
-// atoms, and the ns lane groups split each window's list into equal
-// contiguous shares (the home cell's entries, which include the atoms
-// themselves, by stride with the exact cutoff test).  The partial sums are
-// combined in group order, so each atom's force is summed in an order fixed
-// by the box state.  Lane l < nin returns the totals of home atom ib + l.
+// atoms (splatted) and meets one entry pair of the list per trip; the ns lane
+// groups split each window's pairs into equal contiguous shares (the home
+// segment, which holds the atoms themselves, by stride with the exact cutoff
+// test).  The partial sums are combined in a fixed order (halves, then
+// groups), so each atom's force is summed in an order fixed by the box
+// state.  Lane l < nin returns the totals of home atom ib + l.
 template <bool OBS>
 __device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int ib, int lane, float &fx,
                                             float &fy, float &fz, float &uu, float &ww)
@@ -801,41 +851,57 @@ __device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int i
     const int ns = qdiv(32, inv_np);
     const int g = qdiv(lane, inv_np), pi = lane - g * np;
     const bool act = g < ns;
-    Acc2 acc = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)};
-    float2 X = f2splat(0.f), Y = X, Z = X;
+    Acc2 a0 = {f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f), f2splat(0.f)}, a1 = a0;
+    float2 X0 = f2splat(0.f), Y0 = X0, Z0 = X0, X1 = X0, Y1 = X0, Z1 = X0;
     const int n_win = (total + kListAtoms - 1) / kListAtoms;
     for (int w = 0; w < n_win; ++w) {
         if (v.built != w) {   // only when the neighbourhood exceeds one window
             const long long s_abs = v.s_abs;
             int tt = 0;
             const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), v.hx, v.hy, v.hz, lane, tt);
-            build_window(B, (int)(s_abs & 1), c, w * kListAtoms, lane, wa);
+            build_window(B, (int)(s_abs & 1), c, tt, w * kListAtoms, lane, wa);
             if (lane == 0) wa.built = w;
             __syncwarp();
         }
         if (act) {
             if (w == 0) {   // the home atoms sit at the front of window 0
-                const int a0 = ib + 2 * pi, a1 = ib + min(2 * pi + 1, nin - 1);   // odd nin: repeat an atom
-                const float4 q0 = wa.list[a0], q1 = wa.list[a1];
-                X = make_float2(q0.x, q1.x);
-                Y = make_float2(q0.y, q1.y);
-                Z = make_float2(q0.z, q1.z);
+                const float *h0 = list_entry(wa, ib + 2 * pi);
+                const float *h1 = list_entry(wa, ib + min(2 * pi + 1, nin - 1));   // odd nin: repeat
+                X0 = f2splat(h0[0]); Y0 = f2splat(h0[2]); Z0 = f2splat(h0[4]);
+                X1 = f2splat(h1[0]); Y1 = f2splat(h1[2]); Z1 = f2splat(h1[4]);
             }
             const unsigned rcb = __float_as_uint(B.rc2f);
             const float rc2f = B.rc2f, ush = B.ushiftf;
-            const int wn = min(kListAtoms, total - w * kListAtoms);
-            const int hn = w == 0 ? n_home : 0;
-            for (int t = g; t < hn; t += ns) pair2<true, OBS>(X, Y, Z, wa.list[t], rc2f, rcb, ush, acc);
-            const int M = wn - hn;
+            const int wp = min(kListAtoms, total - w * kListAtoms) >> 1;   // entry pairs in the window
+            const int hp = w == 0 ? (n_home + 1) >> 1 : 0;                  // home segment pairs
+            const float4 *L = wa.list;
+            for (int t = g; t < hp; t += ns) {
+                const float4 xy = L[2 * t], zw = L[2 * t + 1];
+                const float2 XJ = make_float2(xy.x, xy.y), YJ = make_float2(xy.z, xy.w), ZJ = make_float2(zw.x, zw.y);
+                pair2<true, OBS>(X0, Y0, Z0, XJ, YJ, ZJ, rc2f, rcb, ush, a0);
+                pair2<true, OBS>(X1, Y1, Z1, XJ, YJ, ZJ, rc2f, rcb, ush, a1);
+            }
+            const int M = wp - hp;
             const int chunk = qdiv(M + ns - 1, inv_of(ns));
-            const float4 *lp = wa.list + hn + g * chunk;
-            const float4 *le = wa.list + hn + min(M, g * chunk + chunk);
-DSEA_UNROLL(DSEA_PAIR_UNROLL_N)
-            for (; lp < le; ++lp) pair2<OBS, OBS>(X, Y, Z, *lp, rc2f, rcb, ush, acc);
+            const float4 *lp = L + 2 * (hp + g * chunk);
+            const float4 *le = L + 2 * (hp + min(M, g * chunk + chunk));
+            DSEA_UNROLL(DSEA_PAIR_UNROLL_N)
+            for (; lp < le; lp += 2) {
+                const float4 xy = lp[0];
+                const float2 ZJ = *reinterpret_cast<const float2 *>(lp + 1);
+                const float2 XJ = make_float2(xy.x, xy.y), YJ = make_float2(xy.z, xy.w);
+                pair2<OBS, OBS>(X0, Y0, Z0, XJ, YJ, ZJ, rc2f, rcb, ush, a0);
+                pair2<OBS, OBS>(X1, Y1, Z1, XJ, YJ, ZJ, rc2f, rcb, ush, a1);
+            }
         }
     }
+    // per lane: home atom 0 of the pair in .x, atom 1 in .y (halves summed)
+    const float2 FX = make_float2(a0.fx.x + a0.fx.y, a1.fx.x + a1.fx.y);
+    const float2 FY = make_float2(a0.fy.x + a0.fy.y, a1.fy.x + a1.fy.y);
+    const float2 FZ = make_float2(a0.fz.x + a0.fz.y, a1.fz.x + a1.fz.y);
+    const float2 UU = make_float2(a0.u.x + a0.u.y, a1.u.x + a1.u.y);
+    const float2 WW = make_float2(a0.w.x + a0.w.y, a1.w.x + a1.w.y);
     // combine the ns partials of each atom pair into lane pi, in group order
-    const float2 FX = acc.fx, FY = acc.fy, FZ = acc.fz, UU = acc.u, WW = acc.w;
     float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
     for (int gg = 1; gg < ns; ++gg) {
         const int src = pi + gg * np;   // < ns * np <= 32
@@ -884,7 +950,12 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
     float vv[3] = {0.f, 0.f, 0.f};
     if (own) {
         slot = wa.hslot[ib + lane];
-        qo = v.total <= kListAtoms ? wa.list[ib + lane] : __ldcg(B.q[p] + slot);
+        if (v.total <= kListAtoms) {
+            const float *f = list_entry(wa, ib + lane);
+            qo = make_float4(f[0], f[2], f[4], f[6]);
+        } else {
+            qo = __ldcg(B.q[p] + slot);
+        }
         aid = __float_as_int(qo.w);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -898,11 +969,13 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             red_u += 0.5 * (double)uu;
             red_w += 0.5 * (double)ww;
             red_k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
-            if (!INTEGRATE) {
+            if (!INTEGRATE) {   // absolute positions: the home cell's centre plus the relative one
                 const long long o = 3LL * aid;
                 B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
                 B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
-                B.out_r[o] = rr[0]; B.out_r[o + 1] = rr[1]; B.out_r[o + 2] = rr[2];
+                B.out_r[o] = ((double)v.hx + 0.5) * B.lc[0] + rr[0];
+                B.out_r[o + 1] = ((double)v.hy + 0.5) * B.lc[1] + rr[1];
+                B.out_r[o + 2] = ((double)v.hz + 0.5) * B.lc[2] + rr[2];
             }
         }
     }
@@ -919,8 +992,7 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             int c3[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
-                c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], wa.ctab + 3 * d, B.lc[d], B.inv_lcf[d],
-                                  B.L[d], B.nc[d], qn[d]);
+                c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], B.lc[d], B.inv_lcf[d], B.nc[d], qn[d]);
             const int dj = qdiv(c3[0], inv_of(B.cps)) - v.j;
             const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
             if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
@@ -949,18 +1021,13 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, d
         const int hx = v.hx, hy = v.hy, hz = v.hz;
         int total = 0;
         const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), hx, hy, hz, lane, total);
-        build_window(B, (int)(s_abs & 1), c, 0, lane, wa);
+        build_window(B, (int)(s_abs & 1), c, total, 0, lane, wa);
         if (lane == 0) {
             wa.n_home = c.n_s + c.n_a;
             wa.hcell = c.gc;
             wa.total = total;
             wa.built = 0;
             wa.n_stay = 0;
-        }
-        if (lane < 9) {
-            const int ax = lane / 3, o = lane - 3 * (lane / 3) - 1;
-            const int cg = ax == 0 ? hx : (ax == 1 ? hy : hz);
-            wa.ctab[lane] = ((double)(cg + o) + 0.5) * B.lc[ax];
         }
         __syncwarp();
     }
@@ -1038,11 +1105,12 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
             if (k >= B.cap) {
                 set_error(B.err, kErrCapacity);
             } else if (PREC == 1) {
-                // FP32 coordinates relative to the centre of the atom's cell
-                const float qx = (float)(x - ((double)cx + 0.5) * B.lc[0]);
-                const float qy = (float)(y - ((double)cy + 0.5) * B.lc[1]);
-                const float qz = (float)(z - ((double)cz + 0.5) * B.lc[2]);
-                store_mixed(B, p, slot, (int)i, x, y, z, (float)vx, (float)vy, (float)vz, qx, qy, qz);
+                // FP64 positions relative to the centre of the atom's cell, and their FP32 copies
+                const double rx = x - ((double)cx + 0.5) * B.lc[0];
+                const double ry = y - ((double)cy + 0.5) * B.lc[1];
+                const double rz = z - ((double)cz + 0.5) * B.lc[2];
+                store_mixed(B, p, slot, (int)i, rx, ry, rz, (float)vx, (float)vy, (float)vz, (float)rx, (float)ry,
+                            (float)rz);
             } else {
                 store_f64(B, p, slot, (int)i, x, y, z, vx, vy, vz);
             }

@@ -81,7 +81,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     const size_t o_desc = take(sizeof(dsea::BoxDev));
     const size_t o_err = take(sizeof(int));
     const size_t o_cnt = take(sizeof(unsigned long long) * 2 * hb.n_cells);   // stayers, arrivals
-    const size_t o_id = take(sizeof(int) * hb.n_slots);
+    const size_t o_id = precision == DSEA_MIXED ? 0 : take(sizeof(int) * hb.n_slots);
     const size_t o_r = take(sizeof(double) * 3 * hb.n_slots);
     const size_t o_v = take((precision == DSEA_MIXED ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots);
     const size_t o_q = precision == DSEA_MIXED ? take(sizeof(float4) * hb.n_slots) : 0;
@@ -98,7 +98,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     for (int q = 0; q < 2; ++q) {   // one configuration: step 0 uses buffer 0 only
         hb.cnt[q] = reinterpret_cast<unsigned long long *>(base + o_cnt);
         hb.arr[q] = hb.cnt[q] + hb.n_cells;
-        hb.id[q] = reinterpret_cast<int *>(base + o_id);
+        hb.id[q] = precision == DSEA_MIXED ? nullptr : reinterpret_cast<int *>(base + o_id);
         hb.r[q] = reinterpret_cast<double *>(base + o_r);
         hb.v[q] = precision == DSEA_MIXED ? nullptr : reinterpret_cast<double *>(base + o_v);
         hb.vf[q] = precision == DSEA_MIXED ? reinterpret_cast<float *>(base + o_v) : nullptr;
