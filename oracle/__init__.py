@@ -6,7 +6,8 @@ CPU-baseline leg of ``bench.py`` may import this package; the library in
 
 * ``lj_oracle.c``   -- plain C, FP64: the pair law and the velocity-Verlet
   loop of Algorithm 1 (Sec. 4), an O(N^2) minimum-image force sum, a
-  27-cell linked-cell force sum and a sampled-subset force sum.
+  27-cell linked-cell force sum and a sampled-subset force sum; each with a
+  periodic x axis or with mirror walls at x = 0 and x = Lx.
 * ``schedule.py``   -- the single-worker stage table (Table 1), Eq. 1 and
   the slice dependency rule of the worker ring (Sec. 3.1, 3.3).
 
@@ -77,8 +78,14 @@ def _configure(lib):
     lib.oracle_forces_cells.argtypes = [i64, p, p, d, p, p, p]
     lib.oracle_forces_subset.argtypes = [i64, p, p, d, i64, p, p, p, p]
     lib.oracle_run.argtypes = [i64, p, p, p, d, d, i64, ctypes.c_int, p, p]
+    c = ctypes.c_int
+    lib.oracle_forces_brute_w.argtypes = [i64, p, p, d, c, p, p, p]
+    lib.oracle_forces_cells_w.argtypes = [i64, p, p, d, c, p, p, p]
+    lib.oracle_forces_subset_w.argtypes = [i64, p, p, d, c, i64, p, p, p, p]
+    lib.oracle_run_w.argtypes = [i64, p, p, p, d, d, i64, c, c, p, p]
     for f in (lib.oracle_pair, lib.oracle_forces_brute, lib.oracle_forces_cells,
-              lib.oracle_forces_subset, lib.oracle_run):
+              lib.oracle_forces_subset, lib.oracle_run, lib.oracle_forces_brute_w,
+              lib.oracle_forces_cells_w, lib.oracle_forces_subset_w, lib.oracle_run_w):
         f.restype = ctypes.c_int
     return lib
 
@@ -103,21 +110,22 @@ def pair(r: float, rc: float = 2.5):
     return f.value, u.value
 
 
-def forces(pos, box, rc: float = 2.5, method: str = "cells"):
+def forces(pos, box, rc: float = 2.5, method: str = "cells", walls: bool = False):
     """Forces (N,3), total pair energy U and virial W = sum_{i<j} r_ij.F_ij.
 
     method: "cells" (27-cell stencil, directed pairs as in Algorithm 1) or
-    "brute" (all unordered pairs, minimum image)."""
+    "brute" (all unordered pairs, minimum image).  walls: mirror walls at
+    x = 0 and x = Lx instead of a periodic x axis (no pair across them)."""
     p = _pos(pos)
     b = np.ascontiguousarray(box, dtype=np.float64)
     F = np.zeros_like(p)
     U, W = ctypes.c_double(), ctypes.c_double()
-    fn = {"cells": _load().oracle_forces_cells, "brute": _load().oracle_forces_brute}[method]
-    _check(fn(len(p), _ptr(p), _ptr(b), rc, _ptr(F), ctypes.byref(U), ctypes.byref(W)))
+    fn = {"cells": _load().oracle_forces_cells_w, "brute": _load().oracle_forces_brute_w}[method]
+    _check(fn(len(p), _ptr(p), _ptr(b), rc, 1 if walls else 0, _ptr(F), ctypes.byref(U), ctypes.byref(W)))
     return F, U.value, W.value
 
 
-def forces_subset(pos, box, idx, rc: float = 2.5):
+def forces_subset(pos, box, idx, rc: float = 2.5, walls: bool = False):
     """Forces (m,3) and per-atom half pair energy / half virial (m,) of the
     atoms idx only, from a 27-cell list over all atoms."""
     p = _pos(pos)
@@ -126,21 +134,23 @@ def forces_subset(pos, box, idx, rc: float = 2.5):
     F = np.zeros((len(ix), 3))
     u = np.zeros(len(ix))
     w = np.zeros(len(ix))
-    _check(_load().oracle_forces_subset(len(p), _ptr(p), _ptr(b), rc, len(ix), _ptr(ix),
-                                        _ptr(F), _ptr(u), _ptr(w)))
+    _check(_load().oracle_forces_subset_w(len(p), _ptr(p), _ptr(b), rc, 1 if walls else 0, len(ix),
+                                          _ptr(ix), _ptr(F), _ptr(u), _ptr(w)))
     return F, u, w
 
 
-def run(pos, vel, box, steps: int, rc: float = 2.5, dt: float = 0.005, method: str = "cells"):
+def run(pos, vel, box, steps: int, rc: float = 2.5, dt: float = 0.005, method: str = "cells",
+        walls: bool = False):
     """Velocity-Verlet NVE run of Algorithm 1.
 
     Returns (pos_n, vel_n, F_n, obs) with obs[s] = (U, W, KE) for s = 0..steps.
-    Positions come back wrapped into [0, L)."""
+    Positions come back wrapped into [0, L).  walls: mirror walls at x = 0
+    and x = Lx (the initial x must lie in [0, Lx))."""
     p = _pos(pos).copy()
     v = _pos(vel).copy()
     b = np.ascontiguousarray(box, dtype=np.float64)
     F = np.zeros_like(p)
     obs = np.zeros((steps + 1, 3))
-    _check(_load().oracle_run(len(p), _ptr(p), _ptr(v), _ptr(b), rc, dt, steps,
-                              1 if method == "cells" else 0, _ptr(F), _ptr(obs)))
+    _check(_load().oracle_run_w(len(p), _ptr(p), _ptr(v), _ptr(b), rc, dt, steps,
+                                1 if method == "cells" else 0, 1 if walls else 0, _ptr(F), _ptr(obs)))
     return p, v, F, obs

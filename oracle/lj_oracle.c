@@ -21,9 +21,15 @@
  *     shifted;
  *   - the virial reported is the physical W = sum_{i<j} r_ij . F_ij, which is
  *     24 times the quantity Algorithm 1 accumulates as V;
- *   - all three axes are periodic with the minimum-image convention (the
- *     workloads ask for a periodic box; Sec. 3 requirement (3) forbids it for
- *     the paper's own ring, see the scheduler notes);
+ *   - by default all three axes are periodic with the minimum-image
+ *     convention (the workloads ask for a periodic box); with walls_x set,
+ *     the x axis instead ends in mirror walls at x = 0 and x = Lx (Sec. 3
+ *     requirement (3) keeps x non-periodic; Sec. 4.2 places a mirror at the
+ *     domain boundaries): no pair interacts across them, and an atom whose
+ *     update takes it past a wall is mirrored back -- its x coordinate is
+ *     reflected in the wall and the x components of its velocity and of the
+ *     force it carries into the next velocity update change sign (a
+ *     specular wall; the paper does not describe the mirror further);
  *   - step 1 of Algorithm 1 starts with F_old := -F(r_0), so the first
  *     velocity update leaves v_0 unchanged and the loop is standard velocity
  *     Verlet; a run of n steps ends with one more force evaluation at r_n and
@@ -74,6 +80,14 @@ static double min_image(double d, double L)
     return ORACLE_MUTANT == 3 ? d : d - L * nearbyint(d / L);
 }
 
+/* Separation along axis `axis`: minimum image, except along x between mirror
+ * walls, where there is no periodic image. */
+static double sep(double d, const double *box, int axis, int walls_x)
+{
+    if (axis == 0 && walls_x && ORACLE_MUTANT != 10) return d;
+    return min_image(d, box[axis]);
+}
+
 /* Pair energy and radial force (positive = repulsive) of one pair at distance
  * r; zero beyond rc.  A closed-form probe of the pair law. */
 int oracle_pair(double r, double rc, double *force_radial, double *energy)
@@ -93,9 +107,10 @@ int oracle_pair(double r, double rc, double *force_radial, double *energy)
 }
 
 /* O(N^2) minimum-image sum over unordered pairs i<j, each pair applied to
- * both atoms (Newton's third law).  F: out, 3n.  U, W: out, totals. */
-int oracle_forces_brute(int64_t n, const double *pos, const double *box, double rc,
-                        double *F, double *U, double *W)
+ * both atoms (Newton's third law).  F: out, 3n.  U, W: out, totals.
+ * walls_x: mirror walls along x (no periodic image along x). */
+int oracle_forces_brute_w(int64_t n, const double *pos, const double *box, double rc, int walls_x,
+                          double *F, double *U, double *W)
 {
     if (n < 0 || !pos || !box || !F || !U || !W || !(rc > 0.0)) return ORACLE_ERR_ARG;
     for (int d = 0; d < 3; ++d)
@@ -105,9 +120,9 @@ int oracle_forces_brute(int64_t n, const double *pos, const double *box, double 
     double u_sum = 0.0, w_sum = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = i + 1; j < n; ++j) {
-            double dx = min_image(pos[3 * i + 0] - pos[3 * j + 0], box[0]);
-            double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], box[1]);
-            double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], box[2]);
+            double dx = sep(pos[3 * i + 0] - pos[3 * j + 0], box, 0, walls_x);
+            double dy = sep(pos[3 * i + 1] - pos[3 * j + 1], box, 1, walls_x);
+            double dz = sep(pos[3 * i + 2] - pos[3 * j + 2], box, 2, walls_x);
             double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= rc2) {
                 double fa, u;
@@ -123,6 +138,12 @@ int oracle_forces_brute(int64_t n, const double *pos, const double *box, double 
     *U = u_sum;
     *W = w_sum;
     return ORACLE_OK;
+}
+
+int oracle_forces_brute(int64_t n, const double *pos, const double *box, double rc, double *F, double *U,
+                        double *W)
+{
+    return oracle_forces_brute_w(n, pos, box, rc, 0, F, U, W);
 }
 
 /* Linked-cell list (a textbook cell list, Sec. 4): cells of edge
@@ -182,8 +203,8 @@ static void free_cells(cell_list *cl)
  * every neighbour j within rc adds r_ij F_abs to F_i, half of the pair energy
  * to U and half of the pair virial to W. */
 static void atom_from_cells(int64_t i, const double *pos, const double *box, double rc2,
-                            double ushift, const cell_list *cl, double *f3, double *u_half,
-                            double *w_half)
+                            double ushift, int walls_x, const cell_list *cl, double *f3,
+                            double *u_half, double *w_half)
 {
     int c0[3];
     for (int d = 0; d < 3; ++d) c0[d] = cell_coord(pos[3 * i + d], box[d], cl->cl[d], cl->nc[d]);
@@ -191,15 +212,16 @@ static void atom_from_cells(int64_t i, const double *pos, const double *box, dou
     for (int ox = -1; ox <= 1; ++ox)
         for (int oy = -1; oy <= 1; ++oy)
             for (int oz = -1; oz <= (ORACLE_MUTANT == 4 ? 0 : 1); ++oz) {
+                if (walls_x && (c0[0] + ox < 0 || c0[0] + ox >= cl->nc[0])) continue; /* beyond a wall */
                 int cx = (c0[0] + ox + cl->nc[0]) % cl->nc[0];
                 int cy = (c0[1] + oy + cl->nc[1]) % cl->nc[1];
                 int cz = (c0[2] + oz + cl->nc[2]) % cl->nc[2];
                 int64_t c = ((int64_t)cx * cl->nc[1] + cy) * cl->nc[2] + cz;
                 for (int64_t j = cl->head[c]; j >= 0; j = cl->next[j]) {
                     if (j == i) continue;
-                    double dx = min_image(pos[3 * i + 0] - pos[3 * j + 0], box[0]);
-                    double dy = min_image(pos[3 * i + 1] - pos[3 * j + 1], box[1]);
-                    double dz = min_image(pos[3 * i + 2] - pos[3 * j + 2], box[2]);
+                    double dx = sep(pos[3 * i + 0] - pos[3 * j + 0], box, 0, walls_x);
+                    double dy = sep(pos[3 * i + 1] - pos[3 * j + 1], box, 1, walls_x);
+                    double dz = sep(pos[3 * i + 2] - pos[3 * j + 2], box, 2, walls_x);
                     double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 <= rc2) {
                         double fa, u;
@@ -220,8 +242,8 @@ static void atom_from_cells(int64_t i, const double *pos, const double *box, dou
 }
 
 /* Cell-list force on every atom (27-cell stencil, directed pairs). */
-int oracle_forces_cells(int64_t n, const double *pos, const double *box, double rc, double *F,
-                        double *U, double *W)
+int oracle_forces_cells_w(int64_t n, const double *pos, const double *box, double rc, int walls_x,
+                          double *F, double *U, double *W)
 {
     if (n < 0 || !pos || !box || !F || !U || !W || !(rc > 0.0)) return ORACLE_ERR_ARG;
     cell_list cl;
@@ -230,7 +252,7 @@ int oracle_forces_cells(int64_t n, const double *pos, const double *box, double 
     double rc2 = rc * rc, ushift = lj_shift(rc), u_sum = 0.0, w_sum = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         double uh, wh;
-        atom_from_cells(i, pos, box, rc2, ushift, &cl, &F[3 * i], &uh, &wh);
+        atom_from_cells(i, pos, box, rc2, ushift, walls_x, &cl, &F[3 * i], &uh, &wh);
         u_sum += uh;
         w_sum += wh;
     }
@@ -240,11 +262,17 @@ int oracle_forces_cells(int64_t n, const double *pos, const double *box, double 
     return ORACLE_OK;
 }
 
+int oracle_forces_cells(int64_t n, const double *pos, const double *box, double rc, double *F, double *U,
+                        double *W)
+{
+    return oracle_forces_cells_w(n, pos, box, rc, 0, F, U, W);
+}
+
 /* Force and per-atom half energy / half virial for a subset of atoms only
  * (idx[0..m-1]); used to check sampled atoms of boxes too large for a full
  * oracle pass.  F: out, 3m; u_atom, w_atom: out, m (may be NULL). */
-int oracle_forces_subset(int64_t n, const double *pos, const double *box, double rc, int64_t m,
-                         const int64_t *idx, double *F, double *u_atom, double *w_atom)
+int oracle_forces_subset_w(int64_t n, const double *pos, const double *box, double rc, int walls_x,
+                           int64_t m, const int64_t *idx, double *F, double *u_atom, double *w_atom)
 {
     if (n < 0 || m < 0 || !pos || !box || !idx || !F || !(rc > 0.0)) return ORACLE_ERR_ARG;
     for (int64_t k = 0; k < m; ++k)
@@ -255,7 +283,7 @@ int oracle_forces_subset(int64_t n, const double *pos, const double *box, double
     double rc2 = rc * rc, ushift = lj_shift(rc);
     for (int64_t k = 0; k < m; ++k) {
         double uh, wh;
-        atom_from_cells(idx[k], pos, box, rc2, ushift, &cl, &F[3 * k], &uh, &wh);
+        atom_from_cells(idx[k], pos, box, rc2, ushift, walls_x, &cl, &F[3 * k], &uh, &wh);
         if (u_atom) u_atom[k] = uh;
         if (w_atom) w_atom[k] = wh;
     }
@@ -263,11 +291,17 @@ int oracle_forces_subset(int64_t n, const double *pos, const double *box, double
     return ORACLE_OK;
 }
 
-static int forces_any(int use_cells, int64_t n, const double *pos, const double *box, double rc,
+int oracle_forces_subset(int64_t n, const double *pos, const double *box, double rc, int64_t m,
+                         const int64_t *idx, double *F, double *u_atom, double *w_atom)
+{
+    return oracle_forces_subset_w(n, pos, box, rc, 0, m, idx, F, u_atom, w_atom);
+}
+
+static int forces_any(int use_cells, int64_t n, const double *pos, const double *box, double rc, int walls_x,
                       double *F, double *U, double *W)
 {
-    return use_cells ? oracle_forces_cells(n, pos, box, rc, F, U, W)
-                     : oracle_forces_brute(n, pos, box, rc, F, U, W);
+    return use_cells ? oracle_forces_cells_w(n, pos, box, rc, walls_x, F, U, W)
+                     : oracle_forces_brute_w(n, pos, box, rc, walls_x, F, U, W);
 }
 
 static double kinetic(int64_t n, const double *vel)
@@ -277,10 +311,27 @@ static double kinetic(int64_t n, const double *vel)
     return 0.5 * s;
 }
 
-static void wrap_positions(int64_t n, double *pos, const double *box)
+/* Mirror walls at x = 0 and x = Lx: an atom past a wall is reflected back,
+ * and the x components of its velocity and of the force it carries into the
+ * next velocity update (F_old) change sign. */
+static void mirror_walls(int64_t n, double *pos, double *vel, double *f_old, const double *box)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double x = pos[3 * i];
+        if (x < 0.0 || x >= box[0]) {
+            pos[3 * i] = x < 0.0 ? -x : 2.0 * box[0] - x;
+            if (ORACLE_MUTANT != 9) {
+                vel[3 * i] = -vel[3 * i];
+                f_old[3 * i] = -f_old[3 * i];
+            }
+        }
+    }
+}
+
+static void wrap_positions(int64_t n, double *pos, const double *box, int walls_x)
 {
     for (int64_t i = 0; i < n; ++i)
-        for (int d = 0; d < 3; ++d) {
+        for (int d = walls_x ? 1 : 0; d < 3; ++d) {
             double x = pos[3 * i + d];
             if (x >= box[d] || x < 0.0) x -= box[d] * floor(x / box[d]);
             if (x >= box[d]) x -= box[d]; /* rounding guard: keep x in [0, L) */
@@ -294,17 +345,25 @@ static void wrap_positions(int64_t n, double *pos, const double *box)
  *   obs:      out, 3 * (steps + 1) doubles (may be NULL): (U, W, KE) at
  *             steps 0..n, each taken where r, v and F are synchronised.
  * Positions are wrapped into the box after every update, the periodic
- * counterpart of storing each molecule in the slice it moved to (Sec. 4.1).
+ * counterpart of storing each molecule in the slice it moved to (Sec. 4.1);
+ * with walls_x the x coordinate is mirrored at the walls instead.  The
+ * initial positions must then lie in [0, Lx).
  */
-int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc, double dt,
-               int64_t steps, int use_cells, double *F, double *obs)
+int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double rc, double dt,
+                 int64_t steps, int use_cells, int walls_x, double *F, double *obs)
 {
     if (n < 0 || steps < 0 || !pos || !vel || !box || !F || !(rc > 0.0)) return ORACLE_ERR_ARG;
     double *f_old = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     if (!f_old) return ORACLE_ERR_OOM;
-    wrap_positions(n, pos, box);
+    if (walls_x)
+        for (int64_t i = 0; i < n; ++i)
+            if (!(pos[3 * i] >= 0.0 && pos[3 * i] < box[0])) {
+                free(f_old);
+                return ORACLE_ERR_ARG;
+            }
+    wrap_positions(n, pos, box, walls_x);
     double U, W;
-    int rcode = forces_any(use_cells, n, pos, box, rc, F, &U, &W); /* F(r_0) */
+    int rcode = forces_any(use_cells, n, pos, box, rc, walls_x, F, &U, &W); /* F(r_0) */
     if (rcode) {
         free(f_old);
         return rcode;
@@ -314,7 +373,7 @@ int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc
     for (int64_t s = 0; s <= steps; ++s) {
         if (s > 0) {
             for (int64_t k = 0; k < 3 * n; ++k) f_old[k] = F[k]; /* F_old = F_new */
-            rcode = forces_any(use_cells, n, pos, box, rc, F, &U, &W); /* F_new = F(r_s) */
+            rcode = forces_any(use_cells, n, pos, box, rc, walls_x, F, &U, &W); /* F_new = F(r_s) */
             if (rcode) break;
         }
         /* second loop of Algorithm 1: v += (F_new + F_old) dt / 2 -> v_s */
@@ -329,8 +388,19 @@ int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc
         /* third loop of Algorithm 1: r += v dt + F_new dt^2 / 2 */
         for (int64_t k = 0; k < 3 * n; ++k)
             pos[k] = pos[k] + vel[k] * dt + (ORACLE_MUTANT == 6 ? 0.0 : F[k] * 0.5 * dt * dt);
-        wrap_positions(n, pos, box);
+        if (walls_x) {
+            /* the force of this step becomes F_old of the next one: carry it
+             * (F_new) through the mirror together with the velocity */
+            mirror_walls(n, pos, vel, F, box);
+        }
+        wrap_positions(n, pos, box, walls_x);
     }
     free(f_old);
     return rcode;
+}
+
+int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc, double dt, int64_t steps,
+               int use_cells, double *F, double *obs)
+{
+    return oracle_run_w(n, pos, vel, box, rc, dt, steps, use_cells, 0, F, obs);
 }

@@ -6,8 +6,9 @@ tests/test_oracle_pins.py fails against it; the unmodified build passes them
 (the pins themselves run in that file).  Planted errors: a dropped factor in
 the force law, the wrong sign of the energy shift, no minimum image, a missing
 layer of neighbour cells, a dropped term of the velocity update, a dropped
-term of the position update, a virial without its r^2 factor, and a strict
-cutoff instead of the inclusive one.
+term of the position update, a virial without its r^2 factor, a strict
+cutoff instead of the inclusive one, a mirror wall that reflects positions but
+not velocities, and pairs that still meet across the mirror walls.
 """
 import os
 
@@ -15,6 +16,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_walls as walls
 
 CASES = {
     1: [lambda: pins.test_pair_law_closed_form(1.0)],
@@ -25,6 +27,8 @@ CASES = {
     6: [pins.test_dimer_trajectory_matches_ode_solver, pins.test_nve_run_conserves_momentum_and_energy],
     7: [pins.test_fcc_lattice_sums],
     8: [pins.test_pair_law_special_points],
+    9: [walls.test_free_flight_into_a_wall_reflects],
+    10: [walls.test_no_pair_across_the_walls],
 }
 
 
