@@ -149,11 +149,11 @@ def flush_l2(buf):
     buf.add_(1.0)      # writes 256 MB > 129 MB L2
 
 
-def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, stream):
+def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, stream, walls=False):
     """Advance one box; returns (seconds over the timed steps, kernel launches,
-    per-step event times)."""
+    per-step event times).  walls: mirror walls along x."""
     pos, vel, box = spec.state()
-    b = dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision, stream=stream)
+    b = dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision, stream=stream, walls=walls)
     try:
         for _ in range(warmup):
             b.advance(md_steps)
@@ -350,7 +350,9 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-window", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
-    ap.add_argument("--skip", default="", help="comma list of legs to skip: fp64,batch,serve,cpu,e2e")
+    ap.add_argument("--skip", default="",
+                    help="comma list of legs to skip: fp64,walls,67m,batch,serve,cpu,e2e")
+    ap.add_argument("--walls-steps", type=int, default=3, help="timed steps of the mirror-wall leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -409,6 +411,15 @@ def main():
         v64 = sum_over_ranks(spec.n_atoms * args.md_steps * args.fp64_steps, world) / sec64
         line["fp64"] = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
                         "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+    if "walls" not in skip:
+        sec_w, _, _, _ = time_box(dsea, torch, spec, dsea.MIXED, args.walls_steps, 3, args.md_steps,
+                                  flush_buf, stream, walls=True)
+        sec_w = max_over_ranks(sec_w, world)
+        v_w = sum_over_ranks(spec.n_atoms * args.md_steps * args.walls_steps, world) / sec_w
+        line["walls"] = {"value": v_w, "unit": UNIT, "steps": args.walls_steps,
+                         "ms_per_step": 1e3 * sec_w / args.walls_steps,
+                         "workload": "the headline box with mirror walls at x = 0 and x = Lx "
+                                     "(DSEA_BOUNDARY_MIRROR), mixed, ring schedule"}
     if "67m" not in skip:
         big = inputs.FLUID_67M
         sec_b, _, _, info_b = time_box(dsea, torch, big, dsea.MIXED, 1, 3, big.steps, flush_buf, stream)

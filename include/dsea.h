@@ -85,6 +85,13 @@ typedef struct {
                           warp in the mixed form); 0 = all that fit */
 } dsea_params;
 
+/* Boundary along x (the slicing axis).  y and z are always periodic. */
+#define DSEA_BOUNDARY_PERIODIC 0 /* minimum image along x as well */
+#define DSEA_BOUNDARY_MIRROR 1   /* specular mirror walls at x = 0 and x = Lx (Sec. 3
+                                    requirement (3); the mirror of Sec. 4.2): no pair
+                                    across them; an atom carried past a wall is
+                                    reflected and its x velocity reversed */
+
 /* A box as the caller describes it (Sec. 4: cubic volume of edge b, but any
  * orthorhombic box works).  n_slices = 0 means one slice per cell layer
  * along x (the paper's choice N_S = N_xyz, Sec. 4). */
@@ -92,8 +99,10 @@ typedef struct {
     int n_slices;
     double box[3];     /* edge lengths Lx, Ly, Lz */
     int64_t n_atoms;
-    const double *pos; /* host, 3 n_atoms, any values (wrapped into the box) */
+    const double *pos; /* host, 3 n_atoms, any values (wrapped into the box); with mirror
+                          walls every x must lie in [0, Lx) */
     const double *vel; /* host, 3 n_atoms, or NULL for zero velocities */
+    int boundary_x;    /* DSEA_BOUNDARY_PERIODIC or DSEA_BOUNDARY_MIRROR */
 } dsea_box_desc;
 
 /* Observables at the box's current step, all FP64:
@@ -115,6 +124,7 @@ typedef struct {
     int64_t n_atoms, step;
     size_t device_bytes;
     double cell_edge[3];
+    int boundary_x;
 } dsea_box_info;
 
 /* ---- box lifecycle ----------------------------------------------------- */

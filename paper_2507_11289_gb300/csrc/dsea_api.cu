@@ -361,6 +361,11 @@ int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, 
     if (desc->n_atoms >= (int64_t)1 << 31) return DSEA_ERR_INVALID_ARG;
     for (int d = 0; d < 3; ++d)
         if (!(desc->box[d] > 0.0) || !std::isfinite(desc->box[d])) return DSEA_ERR_INVALID_ARG;
+    if (desc->boundary_x != DSEA_BOUNDARY_PERIODIC && desc->boundary_x != DSEA_BOUNDARY_MIRROR)
+        return DSEA_ERR_INVALID_ARG;
+    if (desc->boundary_x == DSEA_BOUNDARY_MIRROR)
+        for (int64_t i = 0; i < desc->n_atoms; ++i)
+            if (!(desc->pos[3 * i] >= 0.0 && desc->pos[3 * i] < desc->box[0])) return DSEA_ERR_INVALID_ARG;
     if (allocator && (!allocator->alloc || !allocator->free)) return DSEA_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -376,6 +381,7 @@ int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, 
         b->has_alloc = true;
     }
     b->n_slices_req = desc->n_slices;
+    b->walls_x = desc->boundary_x == DSEA_BOUNDARY_MIRROR ? 1 : 0;
     for (int d = 0; d < 3; ++d) b->L[d] = desc->box[d];
     b->hb.n_atoms = desc->n_atoms;
     b->pos0.assign(desc->pos, desc->pos + 3 * desc->n_atoms);
@@ -401,6 +407,7 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
     BoxDev &hb = b->hb;
     int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
     if (rc0) return rc0;
+    hb.walls_x = b->walls_x;
     const int n_s = hb.n_slices;
     b->params = p;
 
@@ -531,6 +538,7 @@ int dsea_box_get_info(const dsea_box *b, dsea_box_info *o)
     const BoxDev &hb = b->hb;
     o->n_atoms = hb.n_atoms;
     o->step = hb.step;
+    o->boundary_x = b->walls_x ? DSEA_BOUNDARY_MIRROR : DSEA_BOUNDARY_PERIODIC;
     if (!b->registered) return DSEA_OK;
     o->n_slices = hb.n_slices;
     o->cells_per_slice_x = hb.cps;

@@ -15,6 +15,7 @@ struct dsea_box {
     bool has_alloc = false;
     int n_slices_req = 0;
     double L[3] = {0, 0, 0};
+    int walls_x = 0;                  // DSEA_BOUNDARY_MIRROR along x
     std::vector<double> pos0, vel0;   // host copies until the kernel is registered
     bool has_vel = false;
     bool registered = false;

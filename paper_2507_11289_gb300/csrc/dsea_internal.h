@@ -41,6 +41,7 @@ struct BoxDev {
     int tile_y, tile_z, tiles_y, tiles_z, units_per_slice;
     int cap;
     int precision;
+    int walls_x;       // 1: mirror walls at x = 0 and x = Lx (no wrap along x)
     int staged_cells;  // max staged cells of a unit
     int smem_atoms;    // staged atoms the unit's shared memory holds
     int64_t n_cells;

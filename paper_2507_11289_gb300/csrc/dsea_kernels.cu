@@ -354,16 +354,24 @@ __device__ __forceinline__ int cell_of(double x, double inv_lc, int n)
 // by d (FP32).  The cell offset is decided in FP32; r becomes the FP64
 // position relative to the destination cell's centre and qn its FP32 copy.
 // Returns the destination cell, wrapped periodically (a relative position
-// needs no wrap).  Three FP64 operations in the common case.
+// needs no wrap), or, with `mirror`, reflected at the walls of the axis:
+// unwrapped cell u < 0 becomes -1 - u, u >= nc becomes 2 nc - 1 - u, and
+// the relative position changes sign (the caller reverses the velocity).
+// Three FP64 operations in the common case.
 __device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, double lc, float inv_lcf, int nc,
-                                         float &qn)
+                                         bool mirror, float &qn, bool &reflected)
 {
     const int o = (int)floorf(fmaf(q + d, inv_lcf, 0.5f));   // cell offset, usually -1, 0 or 1
     double rn = r + (double)d;                               // FP64 position update
     if (o != 0) rn -= (double)o * lc;                        // rebase on the new cell's centre
+    int c = cg + o;
+    reflected = mirror && (c < 0 || c >= nc);
+    if (reflected) {
+        c = c < 0 ? -1 - c : 2 * nc - 1 - c;
+        rn = -rn;
+    }
     r = rn;
     qn = (float)rn;
-    int c = cg + o;
     c = c < 0 ? c + nc : (c >= nc ? c - nc : c);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
@@ -420,7 +428,9 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         const int gy = wrap_index(y0 - 1 + ly, B.nc[1]);
         const int gz = wrap_index(z0 - 1 + lz, B.nc[2]);
         const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
-        const unsigned long long ws = __ldcg(B.cnt[p] + gc), wa = __ldcg(B.arr[p] + gc);
+        const bool beyond = B.walls_x && (x0 - 1 + lx < 0 || x0 - 1 + lx >= B.nc[0]);   // past a wall
+        const unsigned long long ws = beyond ? 0ull : __ldcg(B.cnt[p] + gc);
+        const unsigned long long wa = beyond ? 0ull : __ldcg(B.arr[p] + gc);
         int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;   // stayers (front)
         int n_a = ((unsigned)(wa >> 32) == tag) ? (int)(unsigned)wa : 0;   // arrivals (back)
         if (n_s + n_a > B.cap) {   // the two ends met: the cell overflowed
@@ -619,7 +629,12 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                     vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
                     vy += kick * fy;
                     vz += kick * fz;
-                    rx = wrap_coord(rx + vx * dt, B.L[0]);   // r(t + dt) = r(t) + v(t + dt/2) dt
+                    rx += vx * dt;   // r(t + dt) = r(t) + v(t + dt/2) dt
+                    if (B.walls_x && (rx < 0.0 || rx >= B.L[0])) {   // mirror at the wall
+                        rx = rx < 0.0 ? -rx : 2.0 * B.L[0] - rx;
+                        vx = -vx;
+                    }
+                    rx = wrap_coord(rx, B.L[0]);
                     ry = wrap_coord(ry + vy * dt, B.L[1]);
                     rz = wrap_coord(rz + vz * dt, B.L[2]);
                     const int cx = cell_of(rx, B.inv_lc[0], B.nc[0]);
@@ -731,9 +746,10 @@ __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag
                                             int lane, int &total)
 {
     NbrCell c = {0, 0, 0, 0, 0.f, 0.f, 0.f};
-    if (lane < 27) {
-        const int kk = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
-        const int ox = kk / 9 - 1, oy = (kk / 3) % 3 - 1, oz = kk % 3 - 1;
+    const int kk = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
+    const int ox = kk / 9 - 1;
+    if (lane < 27 && !(B.walls_x && (hx + ox < 0 || hx + ox >= B.nc[0]))) {   // nothing beyond a wall
+        const int oy = (kk / 3) % 3 - 1, oz = kk % 3 - 1;
         const int gx = wrap_index(hx + ox, B.nc[0]), gy = wrap_index(hy + oy, B.nc[1]),
                   gz = wrap_index(hz + oz, B.nc[2]);
         const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
@@ -990,9 +1006,12 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             const float q3[3] = {qo.x, qo.y, qo.z};
             const int cg[3] = {v.hx, v.hy, v.hz};
             int c3[3];
+            bool refl[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d)   // r(t + dt) = r(t) + v(t + dt/2) dt, in FP64
-                c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], B.lc[d], B.inv_lcf[d], B.nc[d], qn[d]);
+                c3[d] = move_axis(rr[d], q3[d], vv[d] * dtf, cg[d], B.lc[d], B.inv_lcf[d], B.nc[d],
+                                  d == 0 && B.walls_x, qn[d], refl[d]);
+            if (refl[0]) vv[0] = -vv[0];   // reflected at a mirror wall
             const int dj = qdiv(c3[0], inv_of(B.cps)) - v.j;
             const int djm = dj < -1 ? dj + B.n_slices : (dj > 1 ? dj - B.n_slices : dj);
             if (djm < -1 || djm > 1) set_error(B.err, kErrMigration);
@@ -1261,6 +1280,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(Rin
                     const unsigned need = (unsigned)ups * (unsigned)s_rel;
                     const unsigned long long t0 = global_ns();
                     for (int d = -2; d <= 2 && go == 1; ++d) {
+                        if (sB.walls_x && (j + d < 0 || j + d >= sB.n_slices)) continue;   // no slice past a wall
                         const int k = wrap_index(j + d, sB.n_slices);
                         unsigned sleep = 32;
                         while (ld_acquire(sB.done + k) < need) {
@@ -1359,6 +1379,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
                 const unsigned need = (unsigned)ups * (unsigned)s_rel;
                 const unsigned long long t0 = global_ns();
                 for (int d = -2; d <= 2 && go == 1; ++d) {
+                    if (B.walls_x && (j + d < 0 || j + d >= B.n_slices)) continue;   // no slice past a wall
                     const int k = wrap_index(j + d, B.n_slices);
                     unsigned sleep = 32;
                     while (ld_acquire(B.done + k) < need) {

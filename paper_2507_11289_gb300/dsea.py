@@ -33,6 +33,8 @@ FP64 = 0
 MIXED = 1
 KERNEL_LJ_TS = 1
 SCHED_RING = 0
+BOUNDARY_PERIODIC = 0
+BOUNDARY_MIRROR = 1
 SCHED_STEPWISE = 1
 DEBUG_WITHHOLD_SLICE = 1
 DEBUG_WAIT_LIMIT_NS = 2
@@ -53,7 +55,7 @@ class Params(ctypes.Structure):
 
 class BoxDesc(ctypes.Structure):
     _fields_ = [("n_slices", ctypes.c_int), ("box", ctypes.c_double * 3), ("n_atoms", ctypes.c_int64),
-                ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p)]
+                ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("boundary_x", ctypes.c_int)]
 
 
 class Observables(ctypes.Structure):
@@ -67,7 +69,7 @@ class BoxInfo(ctypes.Structure):
                 ("units_per_step", ctypes.c_int), ("cell_capacity", ctypes.c_int),
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("n_atoms", ctypes.c_int64),
                 ("step", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("cell_edge", ctypes.c_double * 3)]
+                ("cell_edge", ctypes.c_double * 3), ("boundary_x", ctypes.c_int)]
 
 
 class DseaError(RuntimeError):
@@ -199,21 +201,23 @@ def make_params(rc=2.5, dt=0.005, precision=FP64, schedule=SCHED_RING, tile_y=0,
     return Params(rc, dt, precision, schedule, tile_y, tile_z, cell_capacity, ctas)
 
 
-def _desc(pos, vel, box, n_slices):
+def _desc(pos, vel, box, n_slices, walls=False):
     p = _f64(pos)
     v = None if vel is None else _f64(vel, len(p))
     d = BoxDesc(int(n_slices), (ctypes.c_double * 3)(*[float(x) for x in box]), len(p),
-                p.ctypes.data, None if v is None else v.ctypes.data)
+                p.ctypes.data, None if v is None else v.ctypes.data,
+                BOUNDARY_MIRROR if walls else BOUNDARY_PERIODIC)
     return d, (p, v)
 
 
 # ---- box lifecycle --------------------------------------------------------
 
-def box_create(pos, vel, box, n_slices: int = 0, stream=None, allocator="torch"):
+def box_create(pos, vel, box, n_slices: int = 0, stream=None, allocator="torch", walls=False):
     """dsea_box_create.  allocator: "torch" (caching allocator), None (cudaMalloc)
-    or a TorchAllocator.  Returns an opaque handle (keep it for every call)."""
+    or a TorchAllocator.  walls: mirror walls at x = 0 and x = Lx instead of a
+    periodic x axis.  Returns an opaque handle (keep it for every call)."""
     lib = load()
-    d, keep = _desc(pos, vel, box, n_slices)
+    d, keep = _desc(pos, vel, box, n_slices, walls)
     sh = _stream_handle(stream)
     alloc = None
     if allocator == "torch":
@@ -333,8 +337,8 @@ def server_create(mem_budget_bytes: int, params: Params | None = None, segment_s
     return s.value
 
 
-def server_submit(srv, pos, vel, box, steps: int, n_slices: int = 0) -> int:
-    d, keep = _desc(pos, vel, box, n_slices)
+def server_submit(srv, pos, vel, box, steps: int, n_slices: int = 0, walls=False) -> int:
+    d, keep = _desc(pos, vel, box, n_slices, walls)
     jid = ctypes.c_uint64()
     _check(load().dsea_server_submit(srv, ctypes.byref(d), int(steps), ctypes.byref(jid)),
            "dsea_server_submit")
@@ -393,8 +397,8 @@ class Box:
 
     def __init__(self, pos, vel, box, n_slices=0, precision=FP64, schedule=SCHED_RING, rc=2.5,
                  dt=0.005, tile_y=0, tile_z=0, cell_capacity=0, ctas=0, stream=None,
-                 allocator="torch"):
-        self.h = box_create(pos, vel, box, n_slices, stream, allocator)
+                 allocator="torch", walls=False):
+        self.h = box_create(pos, vel, box, n_slices, stream, allocator, walls)
         try:
             register_kernel(self.h, make_params(rc, dt, precision, schedule, tile_y, tile_z,
                                                 cell_capacity, ctas))

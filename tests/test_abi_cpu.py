@@ -70,3 +70,20 @@ def test_invalid_arguments_without_gpu():
     with pytest.raises(dsea.DseaError) as e:
         dsea.ring_order(2, 1, 1)            # fewer than three slices
     assert e.value.code == dsea.ERR_INVALID_ARG
+
+
+def test_mirror_walls_reject_atoms_outside_without_gpu():
+    """Box validation runs before any device call: with mirror walls every x
+    must lie in [0, Lx); an unknown boundary code is rejected too."""
+    box = [9.0, 9.0, 9.0]
+
+    def create(desc):
+        h = dsea.ctypes.c_void_p()
+        return dsea.load().dsea_box_create(dsea.ctypes.byref(desc), None, None, dsea.ctypes.byref(h))
+
+    for x in (-0.1, 9.0):
+        d, keep = dsea._desc([[x, 1.0, 1.0]], None, box, 0, walls=True)
+        assert create(d) == dsea.ERR_INVALID_ARG
+    d, keep = dsea._desc([[1.0, 1.0, 1.0]], None, box, 0)
+    d.boundary_x = 7
+    assert create(d) == dsea.ERR_INVALID_ARG
