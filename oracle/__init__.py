@@ -83,9 +83,12 @@ def _configure(lib):
     lib.oracle_forces_cells_w.argtypes = [i64, p, p, d, c, p, p, p]
     lib.oracle_forces_subset_w.argtypes = [i64, p, p, d, c, i64, p, p, p, p]
     lib.oracle_run_w.argtypes = [i64, p, p, p, d, d, i64, c, c, p, p]
+    lib.oracle_run_ex.argtypes = [i64, p, p, p, d, d, i64, c, c, c, c, d, p, p, p]
+    lib.oracle_profiles.argtypes = [i64, p, p, p, d, c, c, c, p]
     for f in (lib.oracle_pair, lib.oracle_forces_brute, lib.oracle_forces_cells,
               lib.oracle_forces_subset, lib.oracle_run, lib.oracle_forces_brute_w,
-              lib.oracle_forces_cells_w, lib.oracle_forces_subset_w, lib.oracle_run_w):
+              lib.oracle_forces_cells_w, lib.oracle_forces_subset_w, lib.oracle_run_w,
+              lib.oracle_run_ex, lib.oracle_profiles):
         f.restype = ctypes.c_int
     return lib
 
@@ -154,3 +157,35 @@ def run(pos, vel, box, steps: int, rc: float = 2.5, dt: float = 0.005, method: s
     _check(_load().oracle_run_w(len(p), _ptr(p), _ptr(v), _ptr(b), rc, dt, steps,
                                 1 if method == "cells" else 0, 1 if walls else 0, _ptr(F), _ptr(obs)))
     return p, v, F, obs
+
+
+def run_nvt(pos, vel, box, steps: int, n_cells_x: int, cells_per_slice: int, temperature: float,
+            rc: float = 2.5, dt: float = 0.005, method: str = "cells", walls: bool = False):
+    """Velocity-Verlet run with the slice thermostat (temperature > 0; 0 = NVE).
+
+    Slices: n_cells_x cell layers of width Lx / n_cells_x along x, cells_per_slice
+    per slice.  Returns (pos_n, vel_n, F_n, obs, stats) with obs[s] = (U, W, KE)
+    and stats[s, j] = (KE_j, N_j) of slice j at step s before that step's scaling."""
+    p = _pos(pos).copy()
+    v = _pos(vel).copy()
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    F = np.zeros_like(p)
+    obs = np.zeros((steps + 1, 3))
+    ns = n_cells_x // cells_per_slice
+    stats = np.zeros((steps + 1, ns, 2))
+    _check(_load().oracle_run_ex(len(p), _ptr(p), _ptr(v), _ptr(b), rc, dt, steps,
+                                 1 if method == "cells" else 0, 1 if walls else 0, n_cells_x,
+                                 cells_per_slice, temperature, _ptr(F), _ptr(obs), _ptr(stats)))
+    return p, v, F, obs, stats
+
+
+def profiles(pos, vel, box, n_cells_x: int, cells_per_slice: int, rc: float = 2.5, walls: bool = False):
+    """Per-slice (U_j, W_j, KE_j, N_j): half pair energies, half pair virials and
+    kinetic energies of the atoms of each slice, and their count."""
+    p = _pos(pos)
+    v = None if vel is None else _pos(vel)
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    out = np.zeros((n_cells_x // cells_per_slice, 4))
+    _check(_load().oracle_profiles(len(p), _ptr(p), None if v is None else _ptr(v), _ptr(b), rc,
+                                   1 if walls else 0, n_cells_x, cells_per_slice, _ptr(out)))
+    return out

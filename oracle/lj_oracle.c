@@ -349,16 +349,110 @@ static void wrap_positions(int64_t n, double *pos, const double *box, int walls_
  * with walls_x the x coordinate is mirrored at the walls instead.  The
  * initial positions must then lie in [0, Lx).
  */
-int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double rc, double dt,
-                 int64_t steps, int use_cells, int walls_x, double *F, double *obs)
+/* Slice of an atom at x: the cell layer floor(x / l) of nc_x layers of
+ * width l = Lx / nc_x (computed as x * (1 / l)), clamped into the box, and the
+ * slice holding that layer among slices of cps layers each. */
+static int slice_of(double x, double Lx, int nc_x, int cps)
+{
+    double inv = 1.0 / (Lx / nc_x);
+    int c = (int)(x * inv);
+    if (c < 0) c = 0;
+    if (c >= nc_x) c = nc_x - 1;
+    return c / cps;
+}
+
+/* The slice thermostat (md_thermo_a/b, md_v3b, Sec. 4.1), read as velocity
+ * scaling per slice with the factor taken from the previous step: the
+ * synchronised velocities of the atoms of slice j at step s are multiplied by
+ * lambda_j(s) = sqrt(T0 / T'_j(s-1)), where T'_j(s-1) = 2 lambda_j(s-1)^2
+ * KE_j(s-1) / (3 N_j(s-1)) is the temperature slice j reached after the
+ * previous step's scaling (KE_j, N_j measured before it).  lambda = 1 at the
+ * first step and after an empty slice.  lam: in, lambda_j(s-1); out,
+ * lambda_j(s). */
+static void slice_thermostat(int64_t n, const double *pos, double *vel, const double *box, int nc_x, int cps,
+                             double T0, const double *prev /* [n_slices][2]: KE, N */, double *lam)
+{
+    int ns = nc_x / cps;
+    for (int j = 0; j < ns; ++j) {
+        double ke = prev[2 * j], cnt = prev[2 * j + 1];
+        double ke_after = (ORACLE_MUTANT == 11 ? 1.0 : lam[j] * lam[j]) * ke;
+        lam[j] = (cnt > 0.0 && ke_after > 0.0) ? sqrt(T0 * 3.0 * cnt / (2.0 * ke_after)) : 1.0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int j = slice_of(pos[3 * i], box[0], nc_x, cps);
+        for (int d = 0; d < 3; ++d) vel[3 * i + d] *= lam[j];
+    }
+}
+
+/* Kinetic energy and atom count of every slice (out: [n_slices][2]). */
+static void slice_stats(int64_t n, const double *pos, const double *vel, const double *box, int nc_x, int cps,
+                        double *out)
+{
+    int ns = nc_x / cps;
+    for (int j = 0; j < 2 * ns; ++j) out[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int j = slice_of(pos[3 * i], box[0], nc_x, cps);
+        double v2 = 0.0;
+        for (int d = 0; d < 3; ++d) v2 += vel[3 * i + d] * vel[3 * i + d];
+        out[2 * j] += 0.5 * v2;
+        out[2 * j + 1] += 1.0;
+    }
+}
+
+/* Spatially resolved statistics (Sec. 4.2): per slice j, the sum over its
+ * atoms of half their pair energies (U_j), of half their pair virials (W_j),
+ * of their kinetic energies (KE_j), and the atom count N_j; slices as in
+ * slice_of().  out: [n_slices][4] = (U_j, W_j, KE_j, N_j). */
+int oracle_profiles(int64_t n, const double *pos, const double *vel, const double *box, double rc, int walls_x,
+                    int nc_x, int cps, double *out)
+{
+    if (n < 0 || !pos || !box || !out || !(rc > 0.0) || nc_x < 1 || cps < 1 || nc_x % cps != 0)
+        return ORACLE_ERR_ARG;
+    int ns = nc_x / cps;
+    for (int j = 0; j < 4 * ns; ++j) out[j] = 0.0;
+    cell_list cl;
+    int rcode = build_cells(n, pos, box, rc, &cl);
+    if (rcode) return rcode;
+    double rc2 = rc * rc, ushift = lj_shift(rc);
+    for (int64_t i = 0; i < n; ++i) {
+        double f3[3], uh, wh;
+        atom_from_cells(i, pos, box, rc2, ushift, walls_x, &cl, f3, &uh, &wh);
+        int j = slice_of(pos[3 * i], box[0], nc_x, cps);
+        double v2 = 0.0;
+        if (vel)
+            for (int d = 0; d < 3; ++d) v2 += vel[3 * i + d] * vel[3 * i + d];
+        out[4 * j + 0] += (ORACLE_MUTANT == 12 ? 2.0 : 1.0) * uh;
+        out[4 * j + 1] += wh;
+        out[4 * j + 2] += 0.5 * v2;
+        out[4 * j + 3] += 1.0;
+    }
+    free_cells(&cl);
+    return ORACLE_OK;
+}
+
+/* Velocity-Verlet run with the optional slice thermostat (NVT when T0 > 0)
+ * and mirror walls.  nc_x / cps define the slices (nc_x cell layers along x,
+ * cps layers per slice); stats (may be NULL) receives, for steps 0..n,
+ * [s][j][2] = (KE_j, N_j) of every slice before that step's scaling. */
+int oracle_run_ex(int64_t n, double *pos, double *vel, const double *box, double rc, double dt,
+                  int64_t steps, int use_cells, int walls_x, int nc_x, int cps, double T0, double *F,
+                  double *obs, double *stats)
 {
     if (n < 0 || steps < 0 || !pos || !vel || !box || !F || !(rc > 0.0)) return ORACLE_ERR_ARG;
+    if (T0 < 0.0 || ((T0 > 0.0 || stats) && (nc_x < 1 || cps < 1 || nc_x % cps != 0))) return ORACLE_ERR_ARG;
+    const int ns = (T0 > 0.0 || stats) ? nc_x / cps : 0;
     double *f_old = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!f_old) return ORACLE_ERR_OOM;
+    double *st = (double *)calloc((size_t)(2 * ns + 2) * 2 + (size_t)ns + 1, sizeof(double)); /* this and the previous step, lambda */
+    if (!f_old || !st) {
+        free(f_old);
+        free(st);
+        return ORACLE_ERR_OOM;
+    }
     if (walls_x)
         for (int64_t i = 0; i < n; ++i)
             if (!(pos[3 * i] >= 0.0 && pos[3 * i] < box[0])) {
                 free(f_old);
+                free(st);
                 return ORACLE_ERR_ARG;
             }
     wrap_positions(n, pos, box, walls_x);
@@ -366,8 +460,11 @@ int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double 
     int rcode = forces_any(use_cells, n, pos, box, rc, walls_x, F, &U, &W); /* F(r_0) */
     if (rcode) {
         free(f_old);
+        free(st);
         return rcode;
     }
+    double *cur = st, *prev = st + (2 * ns + 2), *lam = st + 2 * (2 * ns + 2);
+    for (int j = 0; j < ns; ++j) lam[j] = 1.0;
     /* F_old := -F(r_0): the first velocity update leaves v_0 unchanged. */
     for (int64_t k = 0; k < 3 * n; ++k) f_old[k] = -F[k];
     for (int64_t s = 0; s <= steps; ++s) {
@@ -384,7 +481,18 @@ int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double 
             obs[3 * s + 1] = W;
             obs[3 * s + 2] = kinetic(n, vel);
         }
+        if (ns > 0) {
+            slice_stats(n, pos, vel, box, nc_x, cps, cur);
+            if (stats)
+                for (int j = 0; j < 2 * ns; ++j) stats[(size_t)s * 2 * ns + j] = cur[j];
+        }
         if (s == steps) break; /* closing half kick done: state is (r_n, v_n, F_n) */
+        /* md_v3b: the thermostat scales the synchronised velocities, with the
+         * factors measured at the previous step (none at the first) */
+        if (T0 > 0.0 && s > 0) slice_thermostat(n, pos, vel, box, nc_x, cps, T0, prev, lam);
+        double *t = prev;
+        prev = cur;
+        cur = t;
         /* third loop of Algorithm 1: r += v dt + F_new dt^2 / 2 */
         for (int64_t k = 0; k < 3 * n; ++k)
             pos[k] = pos[k] + vel[k] * dt + (ORACLE_MUTANT == 6 ? 0.0 : F[k] * 0.5 * dt * dt);
@@ -396,7 +504,14 @@ int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double 
         wrap_positions(n, pos, box, walls_x);
     }
     free(f_old);
+    free(st);
     return rcode;
+}
+
+int oracle_run_w(int64_t n, double *pos, double *vel, const double *box, double rc, double dt, int64_t steps,
+                 int use_cells, int walls_x, double *F, double *obs)
+{
+    return oracle_run_ex(n, pos, vel, box, rc, dt, steps, use_cells, walls_x, 0, 0, 0.0, F, obs, NULL);
 }
 
 int oracle_run(int64_t n, double *pos, double *vel, const double *box, double rc, double dt, int64_t steps,

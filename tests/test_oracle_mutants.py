@@ -8,7 +8,9 @@ the force law, the wrong sign of the energy shift, no minimum image, a missing
 layer of neighbour cells, a dropped term of the velocity update, a dropped
 term of the position update, a virial without its r^2 factor, a strict
 cutoff instead of the inclusive one, a mirror wall that reflects positions but
-not velocities, and pairs that still meet across the mirror walls.
+not velocities, pairs that still meet across the mirror walls, a thermostat
+that forgets its own previous scaling, and slice profiles that count whole
+pair energies.
 """
 import os
 
@@ -16,6 +18,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_nvt as nvt
 from tests import test_oracle_walls as walls
 
 CASES = {
@@ -29,6 +32,8 @@ CASES = {
     8: [pins.test_pair_law_special_points],
     9: [walls.test_free_flight_into_a_wall_reflects],
     10: [walls.test_no_pair_across_the_walls],
+    11: [nvt.test_ideal_gas_reaches_the_target_in_one_scaling],
+    12: [lambda: nvt.test_fcc_profiles_are_the_lattice_sums()],
 }
 
 
