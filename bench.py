@@ -149,11 +149,15 @@ def flush_l2(buf):
     buf.add_(1.0)      # writes 256 MB > 129 MB L2
 
 
-def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, stream, walls=False):
+def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, stream, walls=False,
+             temperature=0.0, profiles=False):
     """Advance one box; returns (seconds over the timed steps, kernel launches,
-    per-step event times).  walls: mirror walls along x."""
+    per-step event times, info).  walls: mirror walls along x; temperature: the
+    slice thermostat's target (0 = NVE); profiles: add the final per-slice
+    profiles to info."""
     pos, vel, box = spec.state()
-    b = dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision, stream=stream, walls=walls)
+    b = dsea.Box(pos, vel, box, n_slices=spec.n_slices, precision=precision, stream=stream, walls=walls,
+                 temperature=temperature)
     try:
         for _ in range(warmup):
             b.advance(md_steps)
@@ -173,6 +177,8 @@ def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, s
         per = [a.elapsed_time(c) * 1e-3 for a, c in times]
         launches = steps * math.ceil(md_steps / 4096)
         info = b.info()
+        if profiles:
+            info["profiles"] = b.profiles()
         return sum(per), launches, per, info
     finally:
         b.close()
@@ -351,8 +357,9 @@ def main():
     ap.add_argument("--serve-window", type=float, default=8.0)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--skip", default="",
-                    help="comma list of legs to skip: fp64,walls,67m,batch,serve,cpu,e2e")
+                    help="comma list of legs to skip: fp64,walls,nvt,67m,batch,serve,cpu,e2e")
     ap.add_argument("--walls-steps", type=int, default=3, help="timed steps of the mirror-wall leg")
+    ap.add_argument("--nvt-steps", type=int, default=3, help="timed steps of the thermostat leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -420,6 +427,21 @@ def main():
                          "ms_per_step": 1e3 * sec_w / args.walls_steps,
                          "workload": "the headline box with mirror walls at x = 0 and x = Lx "
                                      "(DSEA_BOUNDARY_MIRROR), mixed, ring schedule"}
+    if "nvt" not in skip:
+        T0 = spec.T
+        sec_t, _, _, info_t = time_box(dsea, torch, spec, dsea.MIXED, args.nvt_steps, 3, args.md_steps,
+                                       flush_buf, stream, temperature=T0, profiles=True)
+        sec_t = max_over_ranks(sec_t, world)
+        v_t = sum_over_ranks(spec.n_atoms * args.md_steps * args.nvt_steps, world) / sec_t
+        pr = info_t["profiles"]
+        t_slice = 2.0 * pr["KE"] / (3.0 * np.maximum(pr["N"], 1))
+        line["nvt"] = {"value": v_t, "unit": UNIT, "steps": args.nvt_steps,
+                       "ms_per_step": 1e3 * sec_t / args.nvt_steps, "target_T": T0,
+                       "slice_T_mean": float(t_slice.mean()), "slice_T_min": float(t_slice.min()),
+                       "slice_T_max": float(t_slice.max()),
+                       "workload": "the headline box under the slice thermostat (NVT, T0 = 1.5), "
+                                   "mixed, ring schedule; slice temperatures from dsea_read_profiles "
+                                   "after the run"}
     if "67m" not in skip:
         big = inputs.FLUID_67M
         sec_b, _, _, info_b = time_box(dsea, torch, big, dsea.MIXED, 1, 3, big.steps, flush_buf, stream)

@@ -83,6 +83,11 @@ typedef struct {
     int cell_capacity; /* atom slots per cell; 0 = from the density */
     int ctas;          /* CTAs of a ring launch (one stage each in the FP64 form, one per
                           warp in the mixed form); 0 = all that fit */
+    double temperature; /* NVT: target kT/epsilon of the slice thermostat (Sec. 4.1,
+                           md_thermo_a/b and md_v3b); 0 = NVE.  Each step scales the
+                           synchronised velocities of slice j by sqrt(T0 / T'_j), T'_j
+                           the slice's temperature after the previous step's scaling
+                           (factor 1 at the first step) */
 } dsea_params;
 
 /* Boundary along x (the slicing axis).  y and z are always periodic. */
@@ -162,6 +167,14 @@ int dsea_read_forces(dsea_box *box, double *out_xyz, int64_t n);
 
 /* Observables at the current step (Algorithm 1's U and V, and KE). */
 int dsea_read_observables(dsea_box *box, dsea_observables *out);
+
+/* Spatially resolved observables at the current step (Sec. 4.2: per-slice
+ * results): for each slice j (n must equal the slice count) the sums over the
+ * atoms of slice j of half their pair energies (U[j]), half their pair
+ * virials (W[j]) and their kinetic energies (KE[j]), and the atom count
+ * (N[j]); host arrays of n entries; any pointer may be NULL.  Slice j holds
+ * the atoms of cell layers [j cps, (j+1) cps) along x.  Synchronising. */
+int dsea_read_profiles(dsea_box *box, double *U, double *W, double *KE, int64_t *N, int n);
 
 int dsea_box_get_info(const dsea_box *box, dsea_box_info *out);
 

@@ -401,8 +401,9 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
     if (!b) return DSEA_ERR_INVALID_ARG;
     if (b->registered) return DSEA_ERR_STATE;
     if (kind != DSEA_KERNEL_LJ_TS || o_in != 1 || o_out != 1) return DSEA_ERR_INVALID_ARG;
-    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0};
+    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0, 0.0};
     if (params) p = *params;
+    if (!(p.temperature >= 0.0) || !std::isfinite(p.temperature)) return DSEA_ERR_INVALID_ARG;
     CU(cudaSetDevice(b->device));
     BoxDev &hb = b->hb;
     int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
@@ -416,7 +417,17 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
     hb.err = (int *)dev_alloc(b, sizeof(int));
     hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * n_s);
     const int64_t max_units = hb.n_cells;   // any tile shape has at most one unit per cell
-    hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * 3 * (size_t)max_units);
+    hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * dsea::kObsStride * (size_t)max_units);
+    hb.T0 = p.temperature;
+    for (int q = 0; q < 2; ++q) {
+        hb.th_part[q] = nullptr;
+        hb.th_lam[q] = nullptr;
+        if (hb.T0 > 0.0) {
+            hb.th_part[q] = (double *)dev_alloc(b, sizeof(double) * 2 * (size_t)max_units);
+            hb.th_lam[q] = (double *)dev_alloc(b, sizeof(double) * n_s);
+            if (!hb.th_part[q] || !hb.th_lam[q]) return DSEA_ERR_OOM;
+        }
+    }
     b->d_obs3 = (double *)dev_alloc(b, sizeof(double) * 3);
     b->d_cum = (int64_t *)dev_alloc(b, sizeof(int64_t) * 2);
     b->d_ticket = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long));
@@ -528,6 +539,34 @@ int dsea_read_observables(dsea_box *b, dsea_observables *out)
     out->U = b->obs3[0];
     out->W = b->obs3[1];
     out->KE = b->obs3[2];
+    return DSEA_OK;
+}
+
+int dsea_read_profiles(dsea_box *b, double *U, double *W, double *KE, int64_t *N, int n)
+{
+    if (!b) return DSEA_ERR_INVALID_ARG;
+    if (!b->registered) return DSEA_ERR_STATE;
+    const BoxDev &hb = b->hb;
+    if (n != hb.n_slices) return DSEA_ERR_INVALID_ARG;
+    int rc = ensure_outputs(b);
+    if (rc) return rc;
+    const int ups = hb.units_per_slice;
+    std::vector<double> part((size_t)dsea::kObsStride * hb.n_slices * ups);
+    CU(cudaMemcpy(part.data(), hb.unit_obs, sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < n; ++j) {   // the slice's units in order
+        double u = 0.0, w = 0.0, k = 0.0, c = 0.0;
+        for (int t = 0; t < ups; ++t) {
+            const double *q = &part[(size_t)dsea::kObsStride * ((size_t)j * ups + t)];
+            u += q[0];
+            w += q[1];
+            k += q[2];
+            c += q[3];
+        }
+        if (U) U[j] = u;
+        if (W) W[j] = w;
+        if (KE) KE[j] = k;
+        if (N) N[j] = (int64_t)c;
+    }
     return DSEA_OK;
 }
 
@@ -936,7 +975,7 @@ void multi_commit(dsea_box *const *boxes, const int64_t *steps, int n)
 int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, size_t *bytes)
 {
     if (!desc || !bytes) return DSEA_ERR_INVALID_ARG;
-    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0};
+    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0, 0.0};
     if (params) p = *params;
     BoxDev hb{};
     double mean_cap = 0;

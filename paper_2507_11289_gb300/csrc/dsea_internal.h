@@ -12,6 +12,7 @@ namespace dsea {
 constexpr int kThreads = 256;            // threads per work-unit CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxStagedCells = 2048;    // staged neighbourhood cells per unit (upper bound)
+constexpr int kObsStride = 4;            // unit partials of a force pass: U, W, KE, atom count
 
 // Device error word values (first error wins).
 enum : int {
@@ -64,7 +65,12 @@ struct BoxDev {
     int withhold_slice;   // testing hook: this slice never reports completion (-1 = off)
     unsigned *done;       // [n_slices] completed units of the running launch
     int *err;             // device error word
-    double *unit_obs;     // [units_per_step * 3] (U, W, KE) partials of a force pass
+    double *unit_obs;     // [units_per_step * kObsStride] (U, W, KE, N) partials of a force pass
+    // slice thermostat (T0 > 0): per unit (KE, N) of the synchronised velocities before
+    // scaling, and per slice the factor applied, both by step parity
+    double T0;
+    double *th_part[2];   // [units_per_step * 2]
+    double *th_lam[2];    // [n_slices]
     double *out_r, *out_v, *out_f;  // readback by atom id, 3 * n_atoms each
     long long wait_limit_ns;        // bounded-wait limit of the ring
 };

@@ -90,7 +90,7 @@ __device__ __forceinline__ float inv_of(int d)
 
 // Shared-memory carve-up of one FP64 unit.
 struct Layout {
-    size_t cnt, nst, start, gcell, atoms, id, slot, scr, red, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, id, slot, scr, red, cellke, lam, ctr, total;
 };
 
 __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
@@ -107,7 +107,9 @@ __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
     L.slot = o;  o += sizeof(int) * smem_atoms;
     o = align16(o);
     L.scr = o;   o += sizeof(double) * kThreads * 5;     // partial sums of split home atoms
-    L.red = o;   o += sizeof(double) * kWarps * 3;
+    L.red = o;   o += sizeof(double) * kWarps * 4;
+    L.cellke = o; o += sizeof(double) * 2 * staged_cells;   // thermostat: (KE, N) per home cell
+    L.lam = o;   o += 16;
     L.ctr = o;   o += 16;
     L.total = align16(o);
     return L;
@@ -116,6 +118,33 @@ __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
 __device__ __forceinline__ int wrap_index(int i, int n)
 {
     return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// The slice thermostat's factor for slice j at step s_abs (Sec. 4.1,
+// md_thermo_a/b): 1 at the first step, else sqrt(T0 / T'), with
+// T' = 2 lam^2 KE / (3 N) the slice's temperature after the previous step's
+// scaling by lam, KE and N summed over the partials the slice's units wrote at
+// that step in a fixed order (lane l takes units l, l + 32, ..., then a
+// butterfly, which leaves the same bits in every lane and every unit).
+// Warp-wide; every lane returns the factor.
+__device__ __forceinline__ double slice_lambda(const BoxDev &B, int j, long long s_abs, bool first_step, int lane)
+{
+    if (first_step) return 1.0;
+    const int q = (int)((s_abs - 1) & 1);
+    const int ups = B.units_per_slice;
+    const double *part = B.th_part[q] + 2LL * j * ups;
+    double ke = 0.0, n = 0.0;
+    for (int t = lane; t < ups; t += 32) {
+        ke += __ldcg(part + 2 * t);
+        n += __ldcg(part + 2 * t + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ke += __shfl_xor_sync(kFull, ke, o);
+        n += __shfl_xor_sync(kFull, n, o);
+    }
+    const double lp = __ldcg(B.th_lam[q] + j);
+    const double ke_after = lp * lp * ke;
+    return (n > 0.0 && ke_after > 0.0) ? sqrt(B.T0 * 3.0 * n / (2.0 * ke_after)) : 1.0;
 }
 
 // Force accumulators of one lane (FP64 form).
@@ -404,7 +433,10 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
     int *s_gcell = reinterpret_cast<int *>(smem + Ly.gcell);
     int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
     double *s_red = reinterpret_cast<double *>(smem + Ly.red);
+    double *s_cellke = reinterpret_cast<double *>(smem + Ly.cellke);
+    double *s_lam = reinterpret_cast<double *>(smem + Ly.lam);
     int *s_ctr = reinterpret_cast<int *>(smem + Ly.ctr);
+    const bool thermo = INTEGRATE && B.T0 > 0.0;   // uniform across the CTA
     double *s_x = reinterpret_cast<double *>(smem + Ly.atoms);
     double *s_y = s_x + B.smem_atoms;
     double *s_z = s_y + B.smem_atoms;
@@ -538,14 +570,19 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             }
         }
     }
+    if (thermo && warp == 0) {   // the slice thermostat's factor of this step
+        const double l = slice_lambda(B, j, s_abs, first_step, lane);
+        if (lane == 0) *s_lam = l;
+    }
     __syncthreads();
 
     // 4./5. forces, then kick, drift and rebin, warp per home cell.  Without
     // a reduction the home cells are handed out dynamically; with one, in a
     // fixed order so that the unit's partial sums are reproducible.
-    double red_u = 0.0, red_w = 0.0, red_k = 0.0;
+    double red_u = 0.0, red_w = 0.0, red_k = 0.0, red_n = 0.0;
     const int n_home = nx * ny * nz;
     const int pn = p ^ 1;
+    const double lam = thermo ? *s_lam : 1.0;
     const unsigned tag_next = tag + 1u;
     const double dt = B.dt;
     const double kick = first_step ? 0.5 * dt : dt;
@@ -561,6 +598,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         const int hs = s_start[kh];
         const long long hcell = s_gcell[kh];
         int n_stay = 0;   // atoms of this cell that stay in it, written to its front slots in order
+        double cell_ke = 0.0;   // thermostat: the cell's KE before scaling, chunks in order
         for (int ib = 0; ib < n_i; ib += 32) {
             const int nin = min(32, n_i - ib);
             const float inv_nin = inv_of(nin);
@@ -615,6 +653,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                     red_u += 0.5 * uu;
                     red_w += 0.5 * ww;
                     red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
+                    red_n += 1.0;
                     if (!INTEGRATE) {
                         const long long o = 3LL * aid;
                         B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
@@ -623,12 +662,29 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                     }
                 }
             }
+            if (thermo) {
+                // synchronised v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start), its KE,
+                // then v(t + dt/2) = lam v(t) + F dt/2 (md_v3b)
+                double ke = 0.0;
+                if (own) {
+                    const double hk = first_step ? 0.0 : 0.5 * dt;
+                    const double sx = vx + hk * fx, sy = vy + hk * fy, sz = vz + hk * fz;
+                    ke = 0.5 * (sx * sx + sy * sy + sz * sz);
+                    vx = lam * sx + 0.5 * dt * fx;
+                    vy = lam * sy + 0.5 * dt * fy;
+                    vz = lam * sz + 0.5 * dt * fz;
+                }
+                for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(kFull, ke, o);
+                cell_ke += ke;
+            }
             if (INTEGRATE) {
                 long long dest = 0;
                 if (own) {
-                    vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
-                    vy += kick * fy;
-                    vz += kick * fz;
+                    if (!thermo) {
+                        vx += kick * fx;   // v(t + dt/2) = v(t - dt/2) + F dt
+                        vy += kick * fy;
+                        vz += kick * fz;
+                    }
                     rx += vx * dt;   // r(t + dt) = r(t) + v(t + dt/2) dt
                     if (B.walls_x && (rx < 0.0 || rx >= B.L[0])) {   // mirror at the wall
                         rx = rx < 0.0 ? -rx : 2.0 * B.L[0] - rx;
@@ -653,11 +709,29 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         // every home cell publishes how many atoms stayed in it, empty or not
         if (INTEGRATE && lane == 0)
             B.cnt[pn][hcell] = ((unsigned long long)tag_next << 32) | (unsigned long long)n_stay;
+        if (thermo && lane == 0) {
+            s_cellke[2 * h] = cell_ke;
+            s_cellke[2 * h + 1] = (double)n_i;
+        }
         if (OBS) {
             h += kWarps;
         } else {
             if (lane == 0) h = atomicAdd(s_ctr, 1);
             h = __shfl_sync(kFull, h, 0);
+        }
+    }
+    if (thermo) {   // the unit's (KE, N) before scaling, home cells in order, and the factor
+        __syncthreads();
+        if (tid == 0) {
+            double ke = 0.0, n = 0.0;
+            for (int q = 0; q < n_home; ++q) {
+                ke += s_cellke[2 * q];
+                n += s_cellke[2 * q + 1];
+            }
+            const long long u = (long long)j * B.units_per_slice + tile;
+            B.th_part[p][2 * u] = ke;
+            B.th_part[p][2 * u + 1] = n;
+            B.th_lam[p][j] = lam;
         }
     }
     if (OBS) {
@@ -666,23 +740,27 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             red_u += __shfl_xor_sync(kFull, red_u, o);
             red_w += __shfl_xor_sync(kFull, red_w, o);
             red_k += __shfl_xor_sync(kFull, red_k, o);
+            red_n += __shfl_xor_sync(kFull, red_n, o);
         }
         if (lane == 0) {
-            s_red[warp * 3 + 0] = red_u;
-            s_red[warp * 3 + 1] = red_w;
-            s_red[warp * 3 + 2] = red_k;
+            s_red[warp * 4 + 0] = red_u;
+            s_red[warp * 4 + 1] = red_w;
+            s_red[warp * 4 + 2] = red_k;
+            s_red[warp * 4 + 3] = red_n;
         }
         __syncthreads();
         if (tid == 0) {
-            double u = 0, w = 0, k = 0;
+            double u = 0, w = 0, k = 0, n = 0;
             for (int q = 0; q < kWarps; ++q) {
-                u += s_red[q * 3];
-                w += s_red[q * 3 + 1];
-                k += s_red[q * 3 + 2];
+                u += s_red[q * 4];
+                w += s_red[q * 4 + 1];
+                k += s_red[q * 4 + 2];
+                n += s_red[q * 4 + 3];
             }
-            B.unit_obs[3LL * unit_id] = u;
-            B.unit_obs[3LL * unit_id + 1] = w;
-            B.unit_obs[3LL * unit_id + 2] = k;
+            B.unit_obs[(long long)kObsStride * unit_id] = u;
+            B.unit_obs[(long long)kObsStride * unit_id + 1] = w;
+            B.unit_obs[(long long)kObsStride * unit_id + 2] = k;
+            B.unit_obs[(long long)kObsStride * unit_id + 3] = n;
         }
     }
 }
@@ -722,6 +800,13 @@ struct WarpArea {
     int hx, hy, hz;            // home cell coordinates
     int n_home, total, built;  // home atoms, list length (padded), window held by the list
     int n_stay;                // atoms that stayed in the home cell so far
+    double lam;                // slice thermostat: the factor of this step (1 without)
+    double ke_acc, n_acc;      // slice thermostat: the unit's KE before scaling, and atoms
+};
+
+// Per-lane FP64 accumulators of a force pass: U, W and KE halves, atoms.
+struct ObsAcc {
+    double u, w, k, n;
 };
 
 // Entry e of the list window: its x (y, z and the id bits follow at +2,
@@ -944,11 +1029,12 @@ __device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int i
 
 // Kick, drift and rebin (INTEGRATE) or read back (OBS without INTEGRATE) the
 // home atoms [ib, ib + 32) of the warp's home cell, given their forces;
-// OBS adds their U, W and KE halves to red_*.
+// OBS adds their U, W and KE halves and their count to red.  With the slice
+// thermostat, the synchronised velocity is scaled by wa.lam before the drift
+// (md_v3b) and its KE before scaling is added to the unit's total.
 template <bool INTEGRATE, bool OBS>
 __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int ib, int lane, float fx, float fy,
-                                            float fz, float uu, float ww, double &red_u, double &red_w,
-                                            double &red_k)
+                                            float fz, float uu, float ww, ObsAcc &red)
 {
     const volatile WarpArea &v = wa;
     const long long s_abs = v.s_abs;
@@ -982,9 +1068,10 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             // synchronised velocity v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start)
             const float hk = first_step ? 0.f : 0.5f * dtf;
             const float sx = fmaf(hk, fx, vv[0]), sy = fmaf(hk, fy, vv[1]), sz = fmaf(hk, fz, vv[2]);
-            red_u += 0.5 * (double)uu;
-            red_w += 0.5 * (double)ww;
-            red_k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+            red.u += 0.5 * (double)uu;
+            red.w += 0.5 * (double)ww;
+            red.k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+            red.n += 1.0;
             if (!INTEGRATE) {   // absolute positions: the home cell's centre plus the relative one
                 const long long o = 3LL * aid;
                 B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
@@ -995,14 +1082,34 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             }
         }
     }
+    if (INTEGRATE && B.T0 > 0.0) {
+        // synchronised v(t) = v(t - dt/2) + F dt/2 (v(t0) itself at the start), its KE,
+        // then v(t + dt/2) = lam v(t) + F dt/2 (md_v3b)
+        double ke = 0.0;
+        if (own) {
+            const float hk = first_step ? 0.f : 0.5f * dtf, lamf = (float)v.lam;
+            const float sx = fmaf(hk, fx, vv[0]), sy = fmaf(hk, fy, vv[1]), sz = fmaf(hk, fz, vv[2]);
+            ke = 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
+            vv[0] = fmaf(0.5f * dtf, fx, lamf * sx);
+            vv[1] = fmaf(0.5f * dtf, fy, lamf * sy);
+            vv[2] = fmaf(0.5f * dtf, fz, lamf * sz);
+        }
+        for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(kFull, ke, o);
+        if (lane == 0) {
+            wa.ke_acc += ke;
+            wa.n_acc += (double)min(32, n_home - ib);
+        }
+    }
     if (INTEGRATE) {
         long long dest = 0;
         float qn[3] = {0.f, 0.f, 0.f};
         if (own) {
-            const float kf = first_step ? 0.5f * dtf : dtf;
-            vv[0] = fmaf(kf, fx, vv[0]);   // v(t + dt/2) = v(t - dt/2) + F dt
-            vv[1] = fmaf(kf, fy, vv[1]);
-            vv[2] = fmaf(kf, fz, vv[2]);
+            if (!(B.T0 > 0.0)) {
+                const float kf = first_step ? 0.5f * dtf : dtf;
+                vv[0] = fmaf(kf, fx, vv[0]);   // v(t + dt/2) = v(t - dt/2) + F dt
+                vv[1] = fmaf(kf, fy, vv[1]);
+                vv[2] = fmaf(kf, fz, vv[2]);
+            }
             const float q3[3] = {qo.x, qo.y, qo.z};
             const int cg[3] = {v.hx, v.hy, v.hz};
             int c3[3];
@@ -1030,8 +1137,7 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
 // neighbourhood into the list, forces, then home_update per 32 home atoms;
 // INTEGRATE publishes how many atoms stayed in the cell.
 template <bool INTEGRATE, bool OBS>
-__device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, double &red_u, double &red_w,
-                                                double &red_k)
+__device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, ObsAcc &red)
 {
     const int lane = threadIdx.x & 31;
     const volatile WarpArea &v = wa;
@@ -1053,13 +1159,46 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, d
     for (int ib = 0; ib < v.n_home; ib += 32) {
         float fx = 0.f, fy = 0.f, fz = 0.f, uu = 0.f, ww = 0.f;
         home_forces<OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww);
-        home_update<INTEGRATE, OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww, red_u, red_w, red_k);
+        home_update<INTEGRATE, OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww, red);
     }
     // the home cell publishes how many atoms stayed in it, empty or not
     if (INTEGRATE && lane == 0)
         B.cnt[(int)(v.s_abs & 1) ^ 1][v.hcell] = ((unsigned long long)(unsigned)(v.s_abs + 2) << 32) |
                                                   (unsigned long long)(unsigned)v.n_stay;
     __syncwarp();   // the list and slot table are reused by the next home cell
+}
+
+// Before a unit's home cells: the slice thermostat's factor and the unit's
+// accumulators (INTEGRATE with T0 > 0 only).
+template <bool INTEGRATE>
+__device__ __forceinline__ void mixed_unit_begin(const BoxDev &B, WarpArea &wa, int j, long long s_abs,
+                                                 bool first_step, int lane)
+{
+    if (!INTEGRATE || !(B.T0 > 0.0)) return;
+    const double l = slice_lambda(B, j, s_abs, first_step, lane);
+    if (lane == 0) {
+        wa.lam = l;
+        wa.ke_acc = 0.0;
+        wa.n_acc = 0.0;
+    }
+    __syncwarp();
+}
+
+// After a unit's home cells: its (KE, N) before scaling and the factor, for
+// the slice's units of the next step.
+template <bool INTEGRATE>
+__device__ __forceinline__ void mixed_unit_end(const BoxDev &B, WarpArea &wa, int j, int tile, long long s_abs,
+                                               int lane)
+{
+    if (!INTEGRATE || !(B.T0 > 0.0)) return;
+    __syncwarp();
+    if (lane == 0) {
+        const int p = (int)(s_abs & 1);
+        const long long u = (long long)j * B.units_per_slice + tile;
+        B.th_part[p][2 * u] = wa.ke_acc;
+        B.th_part[p][2 * u + 1] = wa.n_acc;
+        B.th_lam[p][j] = wa.lam;
+    }
 }
 
 // Home cell h of unit (j, tile) (z fastest, then y, then x) into wa.hx/hy/hz.
@@ -1169,22 +1308,26 @@ __global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long
         wa.j = j;
         wa.first = first;
     }
-    double red_u = 0.0, red_w = 0.0, red_k = 0.0;
+    ObsAcc red = {0.0, 0.0, 0.0, 0.0};
+    mixed_unit_begin<INTEGRATE>(sB, wa, j, s_abs, first != 0, lane);
     const int n = unit_cell_count(sB, tile);
     for (int h = 0; h < n; ++h) {
         set_unit_cell(sB, wa, j, tile, h);
-        mixed_home_cell<INTEGRATE, OBS>(sB, wa, red_u, red_w, red_k);
+        mixed_home_cell<INTEGRATE, OBS>(sB, wa, red);
     }
+    mixed_unit_end<INTEGRATE>(sB, wa, j, tile, s_abs, lane);
     if (OBS) {   // fixed-order FP64 reduction of the unit: xor tree over the lanes
         for (int o = 16; o > 0; o >>= 1) {
-            red_u += __shfl_xor_sync(kFull, red_u, o);
-            red_w += __shfl_xor_sync(kFull, red_w, o);
-            red_k += __shfl_xor_sync(kFull, red_k, o);
+            red.u += __shfl_xor_sync(kFull, red.u, o);
+            red.w += __shfl_xor_sync(kFull, red.w, o);
+            red.k += __shfl_xor_sync(kFull, red.k, o);
+            red.n += __shfl_xor_sync(kFull, red.n, o);
         }
         if (lane == 0) {
-            sB.unit_obs[3LL * u] = red_u;
-            sB.unit_obs[3LL * u + 1] = red_w;
-            sB.unit_obs[3LL * u + 2] = red_k;
+            sB.unit_obs[(long long)kObsStride * u] = red.u;
+            sB.unit_obs[(long long)kObsStride * u + 1] = red.w;
+            sB.unit_obs[(long long)kObsStride * u + 2] = red.k;
+            sB.unit_obs[(long long)kObsStride * u + 3] = red.n;
         }
     }
 }
@@ -1194,9 +1337,9 @@ __global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int 
     __shared__ double s[3][256];
     double a = 0, b = 0, c = 0;
     for (int i = threadIdx.x; i < n; i += 256) {
-        a += unit_obs[3LL * i];
-        b += unit_obs[3LL * i + 1];
-        c += unit_obs[3LL * i + 2];
+        a += unit_obs[(long long)kObsStride * i];
+        b += unit_obs[(long long)kObsStride * i + 1];
+        c += unit_obs[(long long)kObsStride * i + 2];
     }
     s[0][threadIdx.x] = a;
     s[1][threadIdx.x] = b;
@@ -1326,7 +1469,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
     WarpArea &wa = reinterpret_cast<WarpArea *>(smem)[warp];
     const volatile WarpArea &v = wa;
     BoxDev &B = s_box[warp];
-    double red_u = 0.0, red_w = 0.0, red_k = 0.0;   // unused (no reduction in the ring)
+    ObsAcc red = {0.0, 0.0, 0.0, 0.0};   // unused (no reduction in the ring)
     if (lane == 0) wa.box = -1;
     __syncwarp();
     while (true) {
@@ -1399,11 +1542,13 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
         go = __shfl_sync(kFull, go, 0);
         if (go == 0) break;
         if (go == 1) {
+            mixed_unit_begin<true>(B, wa, v.j, v.s_abs, v.first != 0, lane);
             const int n = unit_cell_count(B, v.tile);
             for (int h = 0; h < n; ++h) {
                 set_unit_cell(B, wa, v.j, v.tile, h);
-                mixed_home_cell<true, false>(B, wa, red_u, red_w, red_k);
+                mixed_home_cell<true, false>(B, wa, red);
             }
+            mixed_unit_end<true>(B, wa, v.j, v.tile, v.s_abs, lane);
         }
         __threadfence();
         __syncwarp();

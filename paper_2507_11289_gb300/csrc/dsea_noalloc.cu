@@ -65,7 +65,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     if (n_atoms < 0 || !box || (n_atoms > 0 && (!pos_dev || !forces_dev))) return DSEA_ERR_INVALID_ARG;
     if (n_atoms >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    dsea_params p{rc, 0.005, precision, DSEA_SCHED_STEPWISE, 0, 0, 0, 0};
+    dsea_params p{rc, 0.005, precision, DSEA_SCHED_STEPWISE, 0, 0, 0, 0, 0.0};
     dsea::BoxDev hb{};
     int rc0 = dsea::box_geometry(0, box, n_atoms, p, hb);
     if (rc0) return rc0;
@@ -85,7 +85,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     const size_t o_r = take(sizeof(double) * 3 * hb.n_slots);
     const size_t o_v = take((precision == DSEA_MIXED ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots);
     const size_t o_q = precision == DSEA_MIXED ? take(sizeof(float4) * hb.n_slots) : 0;
-    const size_t o_obs = take(sizeof(double) * 3 * (size_t)units);
+    const size_t o_obs = take(sizeof(double) * dsea::kObsStride * (size_t)units);
     const size_t o_outr = take(sizeof(double) * n3);
     const size_t o_outv = take(sizeof(double) * n3);
     if (off > kScratchBytes) return DSEA_ERR_SCRATCH_LIMIT;

@@ -196,7 +196,7 @@ int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int s
     dsea_server *s = new (std::nothrow) dsea_server();
     if (!s) return DSEA_ERR_OOM;
     s->budget = mem_budget_bytes;
-    s->params = params ? *params : dsea_params{2.5, 0.005, DSEA_MIXED, DSEA_SCHED_RING, 0, 0, 0, 0};
+    s->params = params ? *params : dsea_params{2.5, 0.005, DSEA_MIXED, DSEA_SCHED_RING, 0, 0, 0, 0, 0.0};
     s->segment = segment_steps;
     s->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&s->device);

@@ -50,7 +50,7 @@ class Allocator(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("rc", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
-                ("cell_capacity", ctypes.c_int), ("ctas", ctypes.c_int)]
+                ("cell_capacity", ctypes.c_int), ("ctas", ctypes.c_int), ("temperature", ctypes.c_double)]
 
 
 class BoxDesc(ctypes.Structure):
@@ -91,6 +91,7 @@ _SIGS = {
     "dsea_read_velocities": (_I, [_P, _P, _I64]),
     "dsea_read_forces": (_I, [_P, _P, _I64]),
     "dsea_read_observables": (_I, [_P, ctypes.POINTER(Observables)]),
+    "dsea_read_profiles": (_I, [_P, _P, _P, _P, _P, _I]),
     "dsea_box_get_info": (_I, [_P, ctypes.POINTER(BoxInfo)]),
     "dsea_box_destroy": (_I, [_P]),
     "dsea_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
@@ -197,8 +198,9 @@ class TorchAllocator:
 
 
 def make_params(rc=2.5, dt=0.005, precision=FP64, schedule=SCHED_RING, tile_y=0, tile_z=0,
-                cell_capacity=0, ctas=0) -> Params:
-    return Params(rc, dt, precision, schedule, tile_y, tile_z, cell_capacity, ctas)
+                cell_capacity=0, ctas=0, temperature=0.0) -> Params:
+    """temperature > 0: NVT with the slice thermostat at that kT/epsilon."""
+    return Params(rc, dt, precision, schedule, tile_y, tile_z, cell_capacity, ctas, float(temperature))
 
 
 def _desc(pos, vel, box, n_slices, walls=False):
@@ -282,6 +284,16 @@ def read_observables(h: Handle) -> dict:
     o = Observables()
     _check(load().dsea_read_observables(h.ptr, ctypes.byref(o)), "dsea_read_observables")
     return {"step": o.step, "U": o.U, "W": o.W, "KE": o.KE}
+
+
+def read_profiles(h: Handle, n_slices: int) -> dict:
+    """dsea_read_profiles: per-slice U, W, KE (half pair energies, half pair
+    virials, kinetic energies of each slice's atoms) and atom counts N."""
+    U, W, KE = (np.zeros(n_slices) for _ in range(3))
+    N = np.zeros(n_slices, dtype=np.int64)
+    _check(load().dsea_read_profiles(h.ptr, U.ctypes.data, W.ctypes.data, KE.ctypes.data, N.ctypes.data,
+                                     int(n_slices)), "dsea_read_profiles")
+    return {"U": U, "W": W, "KE": KE, "N": N}
 
 
 def box_get_info(h: Handle) -> dict:
@@ -397,11 +409,11 @@ class Box:
 
     def __init__(self, pos, vel, box, n_slices=0, precision=FP64, schedule=SCHED_RING, rc=2.5,
                  dt=0.005, tile_y=0, tile_z=0, cell_capacity=0, ctas=0, stream=None,
-                 allocator="torch", walls=False):
+                 allocator="torch", walls=False, temperature=0.0):
         self.h = box_create(pos, vel, box, n_slices, stream, allocator, walls)
         try:
             register_kernel(self.h, make_params(rc, dt, precision, schedule, tile_y, tile_z,
-                                                cell_capacity, ctas))
+                                                cell_capacity, ctas, temperature))
         except Exception:
             box_destroy(self.h)
             raise
@@ -424,6 +436,9 @@ class Box:
 
     def observables(self):
         return read_observables(self.h)
+
+    def profiles(self):
+        return read_profiles(self.h, self.info()["n_slices"])
 
     def info(self):
         return box_get_info(self.h)

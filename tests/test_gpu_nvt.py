@@ -1,0 +1,112 @@
+"""GPU parity of the slice thermostat (NVT) and of the per-slice profiles with
+the oracle (oracle.run_nvt, oracle.profiles).  Tolerances as in the NVE
+parity tests: FP64 trajectory 1e-9 sigma after 100 steps; FP64 profile sums
+1e-12 relative; mixed forms hold the target temperature.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_11289_gb300 import dsea, inputs
+from tests.test_oracle_nvt import _gas
+
+pytestmark = pytest.mark.gpu
+
+RC = 2.5
+
+
+def slices_of(b):
+    inf = b.info()
+    return inf["cells"][0], inf["cells_per_slice_x"]
+
+
+def min_image(d, box):
+    return d - box * np.round(d / box)
+
+
+def test_fp64_nvt_trajectory_matches_oracle(melted_4k):
+    pos, vel, box = melted_4k
+    T0 = 1.1
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.FP64, temperature=T0) as b:
+        ncx, cps = slices_of(b)
+        b.advance(55)
+        b.advance(45)
+        rg, vg, og = b.positions(), b.velocities(), b.observables()
+    ro, vo, Fo, obs, st = oracle.run_nvt(pos, vel, box, 100, ncx, cps, T0)
+    dr = np.abs(min_image(rg - ro, box)).max()
+    dv = np.abs(vg - vo).max()
+    print(f"NVT FP64: max |dr| {dr:.3e}, max |dv| {dv:.3e}")
+    assert dr <= 1e-9 and dv <= 1e-8
+    assert og["KE"] == pytest.approx(obs[-1, 2], rel=1e-10)
+
+
+@pytest.mark.parametrize("precision,tol", [(dsea.FP64, 1e-13), (dsea.MIXED, 1e-6)])
+def test_ideal_gas_slices_reach_the_target_in_one_scaling(precision, tol):
+    temps = [2.0, 0.5, 1.2]
+    pos, vel, box, ncx, cps = _gas(60, temps)
+    with dsea.Box(pos, vel, box, n_slices=3, precision=precision, temperature=1.0) as b:
+        assert slices_of(b) == (ncx, cps)
+        b.advance(40)
+        vg = b.velocities()
+        prof = b.profiles()
+    for j, T in enumerate(temps):
+        sl = slice(60 * j, 60 * (j + 1))
+        assert np.allclose(vg[sl], vel[sl] * math.sqrt(1.0 / T), rtol=tol, atol=tol)
+    assert np.all(prof["N"] == 60)
+    assert np.allclose(2 * prof["KE"] / (3 * prof["N"]), 1.0, rtol=10 * tol)
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_ring_equals_stepwise_with_thermostat(precision, melted_4k):
+    pos, vel, box = melted_4k
+    out = []
+    for sched in (dsea.SCHED_RING, dsea.SCHED_STEPWISE):
+        with dsea.Box(pos, vel, box, n_slices=4, precision=precision, schedule=sched, temperature=1.2) as b:
+            b.advance(20)
+            b.advance(17)
+            out.append((b.positions(), b.velocities()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_mixed_slices_hold_the_target(melted_4k):
+    pos, vel, box = melted_4k
+    T0 = 0.9
+    temps = []
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.MIXED, temperature=T0) as b:
+        b.advance(150)
+        for _ in range(15):
+            b.advance(10)
+            p = b.profiles()
+            temps.append(2 * p["KE"] / (3 * p["N"]))
+    late = np.mean(temps, axis=0)
+    print("mixed NVT slice temperatures", late)
+    assert np.allclose(late, T0, rtol=0.02)
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_profiles_match_oracle(precision, melted_4k):
+    pos, vel, box = melted_4k
+    with dsea.Box(pos, vel, box, n_slices=4, precision=precision) as b:
+        ncx, cps = slices_of(b)
+        pg = b.profiles()
+        ob = b.observables()
+    po = oracle.profiles(pos, vel, box, ncx, cps)
+    assert np.array_equal(pg["N"], po[:, 3].astype(np.int64))
+    tol = 1e-12 if precision == dsea.FP64 else 2e-6
+    F, _, _ = oracle.forces(pos, box, RC)
+    frms = float(np.sqrt((F ** 2).sum(1).mean()))
+    for k, col in (("U", 0), ("W", 1)):
+        assert np.abs(pg[k] - po[:, col]).max() <= tol * len(pos) * frms / 4
+    assert np.allclose(pg["KE"], po[:, 2], rtol=1e-12 if precision == dsea.FP64 else 1e-6)
+    assert pg["U"].sum() == pytest.approx(ob["U"], rel=1e-12)
+    # FP64: after steps too (cells are decided in FP64 like the oracle's slices)
+    if precision == dsea.FP64:
+        with dsea.Box(pos, vel, box, n_slices=4, precision=precision) as b:
+            b.advance(30)
+            pg = b.profiles()
+            rg, vg = b.positions(), b.velocities()
+        po = oracle.profiles(rg, vg, box, ncx, cps)
+        assert np.array_equal(pg["N"], po[:, 3].astype(np.int64))
+        assert np.allclose(pg["U"], po[:, 0], rtol=1e-11)
