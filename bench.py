@@ -184,6 +184,46 @@ def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, s
         b.close()
 
 
+def measured_peaks() -> dict:
+    """The measured peaks (HBM copy GB/s, bf16 TFLOP/s), if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def dataset_run(dsea, torch, stream, n_slices=43, points_per_slice=1 << 21, workers=4, steps=50):
+    """The generic slice ring (dsea_dataset_*) with the library's example
+    kernel, an explicit FP64 heat-equation step on a periodic rod: HBM-bound,
+    16 algorithmic bytes per grid point and step (read and write one value)."""
+    m = points_per_slice
+    ds = dsea.Dataset(n_slices, m * 8, o_in=1, o_out=0, n_workers=workers, stream=stream)
+    try:
+        ds.register("heat1d", 0.2)
+        rng = np.random.Generator(np.random.PCG64(5))
+        for j in range(n_slices):
+            ds.write(j, rng.uniform(-1.0, 1.0, m))
+        ds.run(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ds.run(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    finally:
+        ds.close()
+    pts = n_slices * m * steps
+    gbs = 16.0 * pts / sec / 1e9
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    return {"value": pts / sec, "unit": "grid-point-steps/s", "steps": steps, "seconds": sec,
+            "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "frac_of_measured_hbm": gbs / hbm if hbm else None,
+            "workload": f"generic slice ring: {n_slices} slices x {m} FP64 points, {workers} workers, "
+                        "explicit heat-equation step per slice (O_in = 1)"}
+
+
 def e2e_run(dsea, torch, spec, precision, steps, md_steps, stream):
     """End to end through the C ABI: host pos/vel in, create + bin on the
     device, advance, read positions and velocities back to host arrays."""
@@ -352,12 +392,14 @@ def main():
     ap.add_argument("--ref-md-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--batch-boxes", type=int, default=512)
-    ap.add_argument("--batch-md-steps", type=int, default=200)
+    ap.add_argument("--batch-md-steps", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=8.0)
     ap.add_argument("--serve-window", type=float, default=8.0)
+    ap.add_argument("--serve-rate-sustainable", type=float, default=2.5,
+                    help="arrival rate of the second served run (about 0.7 utilisation)")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--skip", default="",
-                    help="comma list of legs to skip: fp64,walls,nvt,67m,batch,serve,cpu,e2e")
+                    help="comma list of legs to skip: fp64,walls,nvt,67m,batch,serve,dataset,cpu,e2e")
     ap.add_argument("--walls-steps", type=int, default=3, help="timed steps of the mirror-wall leg")
     ap.add_argument("--nvt-steps", type=int, default=3, help="timed steps of the thermostat leg")
     args = ap.parse_args()
@@ -458,6 +500,10 @@ def main():
         line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream)
     if "serve" not in skip:
         line["served"] = serve_run(dsea, torch, args.serve_rate, args.serve_window, args.serve_budget_gb)
+        line["served_sustainable"] = serve_run(dsea, torch, args.serve_rate_sustainable, args.serve_window,
+                                               args.serve_budget_gb)
+    if "dataset" not in skip:
+        line["dataset_heat1d"] = dataset_run(dsea, torch, stream)
     if "e2e" not in skip:
         line["e2e"] = e2e_run(dsea, torch, spec, dsea.MIXED, 3, args.md_steps, stream)
     if rank == 0 and world == 1 and "cpu" not in skip:

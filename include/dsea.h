@@ -280,6 +280,69 @@ int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev, int64_t n_
 #define DSEA_DEBUG_WAIT_LIMIT_NS 2
 int dsea_debug_set(dsea_box *box, int key, int64_t value);
 
+/* ---- the generic slice ring (Sec. 3.1, 3.3) ------------------------------ */
+
+/* A sliced dataset streamed through a registered slice kernel: the paper's
+ * model of "the user provides slices of the dataset" and a kernel with O_in
+ * input and O_out output neighbours (Sec. 3.3, caller_worker), for explicit
+ * algorithms other than the built-in Lennard-Jones step.  Each slice has two
+ * device buffers of slice_bytes (step parity: a step never overwrites its own
+ * inputs, Sec. 3.1).  n_workers CUDA streams are the workers: worker k runs
+ * the steps s = k mod n_workers, each step sweeping every slice once in a
+ * cyclic order that starts (O_in + O_out) s slices further than at step 0;
+ * unit (j, s) starts after units (j - R .. j + R, s - 1), R = O_in + O_out,
+ * which finalise its inputs and are the last readers of the buffers it
+ * overwrites.  Units of one step run one after another, so outputs shared
+ * with neighbouring units (O_out > 0) are never written concurrently. */
+typedef struct dsea_dataset dsea_dataset;
+
+/* A slice kernel ("caller_worker" launcher).  Computes step + 1 from step for
+ * slice `slice` by enqueueing device work on `stream` (a cudaStream_t):
+ *   in[k],  k = 0 .. 2 O_in:  device view of slice (slice - O_in + k) mod n at `step` (read only);
+ *   out[k], k = 0 .. 2 O_out: device view of slice (slice - O_out + k) mod n at step + 1.
+ * out[O_out] is the slice's own output; views of other slices are shared with
+ * their units.  Returns 0, or a negative DSEA_ERR_* that stops the run. */
+typedef int (*dsea_slice_fn)(void *user, int slice, int64_t step, const void *const *in, void *const *out,
+                             size_t slice_bytes, void *stream);
+
+/* Create a dataset of n_slices zero-filled slices (2 (O_in + O_out) + 1 <=
+ * n_slices, 1 <= n_workers <= 64).  allocator: as for boxes (NULL =
+ * cudaMalloc).  cuda_stream: the caller's stream, which runs ordered with
+ * every dsea_dataset_run.  INVALID_ARG, NO_DEVICE, OOM. */
+int dsea_dataset_create(int n_slices, size_t slice_bytes, int o_in, int o_out, int n_workers,
+                        const dsea_allocator *allocator, void *cuda_stream, dsea_dataset **out);
+
+/* Copy host bytes into (out of) slice `slice` at the current step; bytes must
+ * equal slice_bytes.  Synchronising. */
+int dsea_dataset_write_slice(dsea_dataset *ds, int slice, const void *host, size_t bytes);
+int dsea_dataset_read_slice(dsea_dataset *ds, int slice, void *host, size_t bytes);
+
+/* Register the slice kernel (replaces any previous one). */
+int dsea_dataset_register(dsea_dataset *ds, dsea_slice_fn fn, void *user);
+
+/* Enqueue n_steps steps of every slice in the ring order; asynchronous with
+ * respect to the host (the caller's stream waits for them).  STATE without a
+ * registered kernel; a kernel's negative status is returned. */
+int dsea_dataset_run(dsea_dataset *ds, int64_t n_steps);
+
+/* Steps completed (queued) so far; -1 for NULL. */
+int64_t dsea_dataset_step(const dsea_dataset *ds);
+
+int dsea_dataset_destroy(dsea_dataset *ds);
+
+/* The dataset's dispatch order without a GPU: for k = 0 .. n_slices n_steps - 1
+ * the slice, absolute step and worker of the k-th unit, steps start_step .. */
+int dsea_dataset_plan(int n_slices, int o_in, int o_out, int n_workers, int64_t n_steps, int64_t start_step,
+                      int32_t *out_slice, int64_t *out_step, int32_t *out_worker);
+
+/* A slice kernel shipped with the library, for tests and examples: one
+ * explicit FP64 step of the heat equation u_t = u_xx on a periodic rod whose
+ * slices hold slice_bytes / 8 grid values each (O_in = 1, O_out = 0):
+ * u'[i] = u[i] + a (u[i-1] - 2 u[i] + u[i+1]), a = *(const double *)user,
+ * evaluated in that order with no contraction. */
+int dsea_example_heat1d(void *user, int slice, int64_t step, const void *const *in, void *const *out,
+                        size_t slice_bytes, void *stream);
+
 /* ---- host-side schedule introspection (no GPU needed) ------------------- */
 
 /* The order in which the ring dispatches the units of one box: for

@@ -110,6 +110,15 @@ _SIGS = {
     "dsea_debug_set": (_I, [_P, _I, _I64]),
     "dsea_forces_noalloc": (_I, [_P, _P, _I64, _P, _D, _I, _P, _P, _P]),
     "dsea_ring_order": (_I, [_I, _I, _I64, _I64, _P, _P]),
+    "dsea_dataset_create": (_I, [_I, ctypes.c_size_t, _I, _I, _I, _P, _P, ctypes.POINTER(_P)]),
+    "dsea_dataset_write_slice": (_I, [_P, _I, _P, ctypes.c_size_t]),
+    "dsea_dataset_read_slice": (_I, [_P, _I, _P, ctypes.c_size_t]),
+    "dsea_dataset_register": (_I, [_P, _P, _P]),
+    "dsea_dataset_run": (_I, [_P, _I64]),
+    "dsea_dataset_step": (_I64, [_P]),
+    "dsea_dataset_destroy": (_I, [_P]),
+    "dsea_dataset_plan": (_I, [_I, _I, _I, _I, _I64, _I64, _P, _P, _P]),
+    "dsea_example_heat1d": (_I, [_P, _I, _I64, _P, _P, ctypes.c_size_t, _P]),
 }
 
 _lib = None
@@ -448,6 +457,79 @@ class Box:
 
     def close(self):
         box_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---- the generic slice ring ------------------------------------------------
+
+SLICE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+def dataset_plan(n_slices: int, o_in: int, o_out: int, n_workers: int, n_steps: int, start_step: int = 0):
+    """dsea_dataset_plan: (slice, step, worker) of every unit in dispatch order."""
+    n = n_slices * n_steps
+    sl = np.empty(n, dtype=np.int32)
+    st = np.empty(n, dtype=np.int64)
+    wk = np.empty(n, dtype=np.int32)
+    _check(load().dsea_dataset_plan(n_slices, o_in, o_out, n_workers, n_steps, start_step, sl.ctypes.data,
+                                    st.ctypes.data, wk.ctypes.data), "dsea_dataset_plan")
+    return sl, st, wk
+
+
+class Dataset:
+    """A sliced dataset streamed through a registered slice kernel (dsea_dataset_*).
+
+    kernel: "heat1d" (the library's example; user = the coefficient a) or a
+    ctypes function pointer of type SLICE_FN / an address."""
+
+    def __init__(self, n_slices, slice_bytes, o_in=1, o_out=0, n_workers=2, stream=None):
+        self.n_slices, self.slice_bytes = int(n_slices), int(slice_bytes)
+        h = ctypes.c_void_p()
+        _check(load().dsea_dataset_create(self.n_slices, self.slice_bytes, int(o_in), int(o_out),
+                                          int(n_workers), None, _stream_handle(stream), ctypes.byref(h)),
+               "dsea_dataset_create")
+        self.h = h.value
+        self._keep = None
+
+    def register(self, kernel, user=None):
+        if kernel == "heat1d":
+            self._keep = (ctypes.c_double(float(user)),)
+            fn = ctypes.cast(load().dsea_example_heat1d, ctypes.c_void_p).value
+            up = ctypes.addressof(self._keep[0])
+        else:
+            self._keep = (kernel, user)
+            fn = ctypes.cast(kernel, ctypes.c_void_p).value
+            up = user
+        _check(load().dsea_dataset_register(self.h, fn, up), "dsea_dataset_register")
+
+    def write(self, slice_index, data: np.ndarray):
+        a = np.ascontiguousarray(data)
+        _check(load().dsea_dataset_write_slice(self.h, int(slice_index), a.ctypes.data, a.nbytes),
+               "dsea_dataset_write_slice")
+
+    def read(self, slice_index, dtype=np.float64) -> np.ndarray:
+        out = np.empty(self.slice_bytes // np.dtype(dtype).itemsize, dtype=dtype)
+        _check(load().dsea_dataset_read_slice(self.h, int(slice_index), out.ctypes.data, out.nbytes),
+               "dsea_dataset_read_slice")
+        return out
+
+    def run(self, n_steps):
+        _check(load().dsea_dataset_run(self.h, int(n_steps)), "dsea_dataset_run")
+
+    @property
+    def step(self):
+        return load().dsea_dataset_step(self.h)
+
+    def close(self):
+        if self.h:
+            load().dsea_dataset_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

@@ -87,3 +87,37 @@ def test_mirror_walls_reject_atoms_outside_without_gpu():
     d, keep = dsea._desc([[1.0, 1.0, 1.0]], None, box, 0)
     d.boundary_x = 7
     assert create(d) == dsea.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,o_in,o_out,workers,steps", [(7, 1, 0, 1, 5), (9, 1, 1, 3, 7), (5, 2, 0, 2, 4),
+                                                         (43, 1, 1, 4, 6)])
+def test_dataset_plan_is_a_valid_time_skewed_ring(n, o_in, o_out, workers, steps):
+    """The generic ring's dispatch order (Sec. 3.1): every step sweeps each
+    slice once, on worker s mod K; every unit's dependencies (slices j-R..j+R,
+    R = O_in + O_out, of the previous step; Sec. 3.3's rule for O_in = O_out =
+    1 is oracle.schedule.ring_dependencies) come earlier; and each step starts
+    R slices further, so its first unit needs only the first 2R+1 of the
+    previous step."""
+    from oracle import schedule
+    sl, st, wk = dsea.dataset_plan(n, o_in, o_out, workers, steps, start_step=3)
+    R = o_in + o_out
+    pos = {(int(a), int(b)): k for k, (a, b) in enumerate(zip(sl, st))}
+    assert len(pos) == n * steps
+    for k, (j, s, w) in enumerate(zip(sl.tolist(), st.tolist(), wk.tolist())):
+        assert w == s % workers
+        if s == 3:
+            continue
+        deps = [((j + d) % n, s - 1) for d in range(-R, R + 1)]
+        if o_in == 1 and o_out == 1:
+            assert sorted(deps) == sorted((int(a), int(b)) for a, b in schedule.ring_dependencies(j, s, n))
+        assert max(pos[x] for x in deps) < k
+    for s in range(4, 3 + steps):
+        first = pos[(int(sl[(s - 3) * n]), s)]
+        need = max(pos[((int(sl[(s - 3) * n]) + d) % n, s - 1)] for d in range(-R, R + 1))
+        assert need - (s - 4) * n <= 2 * R
+
+
+def test_dataset_plan_rejects_overlapping_views():
+    with pytest.raises(dsea.DseaError) as e:
+        dsea.dataset_plan(4, 1, 1, 1, 1)     # 2 (O_in + O_out) + 1 = 5 views of 4 slices
+    assert e.value.code == dsea.ERR_INVALID_ARG
