@@ -781,7 +781,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
 // There is no unit-wide staging, so warps never wait for each other.
 
 #ifndef DSEA_LIST_ATOMS
-#define DSEA_LIST_ATOMS 352
+#define DSEA_LIST_ATOMS 400
 #endif
 constexpr int kListAtoms = DSEA_LIST_ATOMS;   // list window (entries, even) of one warp
 constexpr int kHomeMax = 128;                 // largest cell capacity (slots of one home cell)
@@ -792,7 +792,7 @@ constexpr float kFarAway = 1.0e4f;            // coordinate of a padding entry (
 // needed, so that no register holds them across the pair loop.
 struct WarpArea {
     float4 list[kListAtoms];   // kListAtoms / 2 entry pairs: [x0 x1 y0 y1], [z0 z1 id0 id1]
-    int hslot[kHomeMax];       // slot of each home atom, in the cell's canonical order
+    unsigned char hslot[kHomeMax];   // slot of each home atom within its cell, canonical order
     long long s_abs;           // step of the input state
     long long hcell;           // home cell
     int j, tile, first;        // unit and first-step flag
@@ -886,7 +886,7 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         const int lo = max(0, w0 - c.pre), hi = min(c.n_s, w1 - c.pre);
         for (int i = lo; i < hi; ++i) {
             cp_async16(&raw[c.pre + i - w0], q + base + i);
-            if (lane == 0) wa.hslot[i] = (int)(base + i);
+            if (lane == 0) wa.hslot[i] = (unsigned char)i;
         }
         // arrivals: slot cap-1-k holds the k-th arrival; order them by id
         const long long abase = base + B.cap - c.n_a;
@@ -904,7 +904,7 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
             const int cp = a0 + r;   // canonical list position
             if (cp >= w0 && cp < w1) {
                 raw[cp - w0] = a;
-                if (lane == 0) wa.hslot[c.n_s + r] = (int)slot;
+                if (lane == 0) wa.hslot[c.n_s + r] = (unsigned char)(B.cap - c.n_a + t);
             }
         }
         // padding: after an odd home cell, and after an odd list
@@ -1051,7 +1051,7 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
     double rr[3] = {0.0, 0.0, 0.0};
     float vv[3] = {0.f, 0.f, 0.f};
     if (own) {
-        slot = wa.hslot[ib + lane];
+        slot = v.hcell * B.cap + wa.hslot[ib + lane];
         if (v.total <= kListAtoms) {
             const float *f = list_entry(wa, ib + lane);
             qo = make_float4(f[0], f[2], f[4], f[6]);
