@@ -336,10 +336,10 @@ int dsea_dataset_plan(int n_slices, int o_in, int o_out, int n_workers, int64_t 
                       int32_t *out_slice, int64_t *out_step, int32_t *out_worker);
 
 /* A slice kernel shipped with the library, for tests and examples: one
- * explicit FP64 step of the heat equation u_t = u_xx on a periodic rod whose
- * slices hold slice_bytes / 8 grid values each (O_in = 1, O_out = 0):
- * u'[i] = u[i] + a (u[i-1] - 2 u[i] + u[i+1]), a = *(const double *)user,
- * evaluated in that order with no contraction. */
+ * explicit FP32 step of the heat equation u_t = u_xx on a periodic rod whose
+ * slices hold slice_bytes / 4 grid values each (O_in = 1, O_out = 0):
+ * u'[i] = u[i] + a (u[i-1] - 2 u[i] + u[i+1]), a = *(const float *)user,
+ * evaluated in that order with every operation rounded (no contraction). */
 int dsea_example_heat1d(void *user, int slice, int64_t step, const void *const *in, void *const *out,
                         size_t slice_bytes, void *stream);
 

@@ -194,9 +194,20 @@ int dsea_dataset_run(dsea_dataset *d, int64_t n_steps)
         const int pin = (int)(s & 1), pout = pin ^ 1;
         for (int i = 0; i < n && rc == DSEA_OK; ++i) {
             const int j = sweep_slice(i, s, n, R);
-            if (s > d->step || d->have_prev)   // the units of step s - 1 this one depends on
-                for (int dlt = -R; dlt <= R; ++dlt)
-                    if (cudaStreamWaitEvent(st, d->ev[pout][wrapi(j + dlt, n)], 0) != cudaSuccess) rc = DSEA_ERR_CUDA;
+            if (s > d->step || d->have_prev) {
+                // the units j - R .. j + R of step s - 1 ran one after another on one
+                // stream: waiting for the one swept last covers all of them
+                int last = wrapi(j - R, n), last_i = -1;
+                for (int dlt = -R; dlt <= R; ++dlt) {
+                    const int jj = wrapi(j + dlt, n);
+                    const int ii = wrapi((int64_t)jj - (int64_t)R * (s - 1), n);   // its sweep position
+                    if (ii > last_i) {
+                        last_i = ii;
+                        last = jj;
+                    }
+                }
+                if (cudaStreamWaitEvent(st, d->ev[pout][last], 0) != cudaSuccess) rc = DSEA_ERR_CUDA;
+            }
             for (int k = 0; k < nin; ++k) in[k] = d->buf[pin][wrapi(j - d->o_in + k, n)];
             for (int k = 0; k < nout; ++k) out[k] = d->buf[pout][wrapi(j - d->o_out + k, n)];
             if (rc == DSEA_OK) {
@@ -252,18 +263,18 @@ namespace {
 
 // One explicit step of u_t = u_xx on a periodic rod cut into equal slices:
 // u'[i] = u[i] + a (u[i-1] - 2 u[i] + u[i+1]), a = dt / dx^2, the end values
-// coming from the neighbouring slices (O_in = 1).  Explicit FP64 roundings
-// (no contraction), so the result matches a plain CPU evaluation bit for bit.
-__global__ void k_heat1d(const double *left, const double *mid, const double *right, double *out, long long m,
-                         double a)
+// coming from the neighbouring slices (O_in = 1).  FP32 with explicit
+// roundings (no contraction), so the result matches a plain CPU evaluation
+// bit for bit; 8 bytes of memory traffic per point and step.
+__global__ void k_heat1d(const float *left, const float *mid, const float *right, float *out, long long m, float a)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const double ul = i > 0 ? mid[i - 1] : left[m - 1];
-        const double ur = i + 1 < m ? mid[i + 1] : right[0];
-        const double u = mid[i];
-        const double lap = __dadd_rn(__dsub_rn(ul, __dmul_rn(2.0, u)), ur);
-        out[i] = __dadd_rn(u, __dmul_rn(a, lap));
+        const float ul = i > 0 ? mid[i - 1] : left[m - 1];
+        const float ur = i + 1 < m ? mid[i + 1] : right[0];
+        const float u = mid[i];
+        const float lap = __fadd_rn(__fsub_rn(ul, __fmul_rn(2.0f, u)), ur);
+        out[i] = __fadd_rn(u, __fmul_rn(a, lap));
     }
 }
 
@@ -274,13 +285,13 @@ extern "C" int dsea_example_heat1d(void *user, int slice, int64_t step, const vo
 {
     (void)slice;
     (void)step;
-    if (!user || !in || !out || slice_bytes % sizeof(double) != 0) return DSEA_ERR_INVALID_ARG;
-    const double a = *static_cast<const double *>(user);
-    const long long m = (long long)(slice_bytes / sizeof(double));
+    if (!user || !in || !out || slice_bytes % sizeof(float) != 0) return DSEA_ERR_INVALID_ARG;
+    const float a = *static_cast<const float *>(user);
+    const long long m = (long long)(slice_bytes / sizeof(float));
     const int threads = 256;
     const long long blocks = std::min<long long>((m + threads - 1) / threads, 152 * 8);
     k_heat1d<<<(int)std::max<long long>(blocks, 1), threads, 0, (cudaStream_t)stream>>>(
-        static_cast<const double *>(in[0]), static_cast<const double *>(in[1]), static_cast<const double *>(in[2]),
-        static_cast<double *>(out[0]), m, a);
+        static_cast<const float *>(in[0]), static_cast<const float *>(in[1]), static_cast<const float *>(in[2]),
+        static_cast<float *>(out[0]), m, a);
     return cudaGetLastError() == cudaSuccess ? 0 : DSEA_ERR_CUDA;
 }

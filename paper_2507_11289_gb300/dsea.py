@@ -499,7 +499,7 @@ class Dataset:
 
     def register(self, kernel, user=None):
         if kernel == "heat1d":
-            self._keep = (ctypes.c_double(float(user)),)
+            self._keep = (ctypes.c_float(float(user)),)
             fn = ctypes.cast(load().dsea_example_heat1d, ctypes.c_void_p).value
             up = ctypes.addressof(self._keep[0])
         else:
@@ -513,7 +513,7 @@ class Dataset:
         _check(load().dsea_dataset_write_slice(self.h, int(slice_index), a.ctypes.data, a.nbytes),
                "dsea_dataset_write_slice")
 
-    def read(self, slice_index, dtype=np.float64) -> np.ndarray:
+    def read(self, slice_index, dtype=np.float32) -> np.ndarray:
         out = np.empty(self.slice_bytes // np.dtype(dtype).itemsize, dtype=dtype)
         _check(load().dsea_dataset_read_slice(self.h, int(slice_index), out.ctypes.data, out.nbytes),
                "dsea_dataset_read_slice")

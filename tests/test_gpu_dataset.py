@@ -1,5 +1,5 @@
 """The generic slice ring (dsea_dataset_*, Sec. 3.1/3.3) on the GPU: the
-library's example slice kernel (an explicit FP64 heat-equation step on a
+library's example slice kernel (an explicit FP32 heat-equation step on a
 periodic rod) streamed over the slices in the time-skewed order equals a
 plain NumPy evaluation of the same update bit for bit, whatever the number of
 workers, the run split and the output radius."""
@@ -14,23 +14,25 @@ pytestmark = pytest.mark.gpu
 
 
 def heat_reference(u0, a, steps):
-    u = u0.copy()
+    """The same update in float32, every operation rounded (NumPy never fuses)."""
+    u = u0.astype(np.float32)
+    a, two = np.float32(a), np.float32(2.0)
     for _ in range(steps):
         ul, ur = np.roll(u, 1), np.roll(u, -1)
-        u = u + a * ((ul - 2.0 * u) + ur)
+        u = u + a * ((ul - two * u) + ur)
     return u
 
 
 def rod(n_slices, m, seed=11):
     rng = np.random.Generator(np.random.PCG64(seed))
-    return rng.uniform(-1.0, 1.0, n_slices * m)
+    return rng.uniform(-1.0, 1.0, n_slices * m).astype(np.float32)
 
 
 @pytest.mark.parametrize("workers", [1, 2, 3])
 def test_heat_ring_equals_numpy_bitwise(workers):
     n, m, a = 7, 1000, 0.23
     u0 = rod(n, m)
-    with dsea.Dataset(n, m * 8, o_in=1, o_out=0, n_workers=workers) as ds:
+    with dsea.Dataset(n, m * 4, o_in=1, o_out=0, n_workers=workers) as ds:
         ds.register("heat1d", a)
         for j in range(n):
             ds.write(j, u0[j * m:(j + 1) * m])
@@ -47,7 +49,7 @@ def test_output_radius_one_through_a_python_kernel():
     n, m, a = 9, 512, 0.2
     u0 = rod(n, m, seed=12)
     lib = dsea.load()
-    coef = ctypes.c_double(a)
+    coef = ctypes.c_float(a)
     calls = []
 
     @dsea.SLICE_FN
@@ -56,7 +58,7 @@ def test_output_radius_one_through_a_python_kernel():
         own = ctypes.c_void_p(out + ctypes.sizeof(ctypes.c_void_p))   # out[O_out] = out[1]
         return lib.dsea_example_heat1d(ctypes.addressof(coef), j, step, inp, own, nbytes, stream)
 
-    with dsea.Dataset(n, m * 8, o_in=1, o_out=1, n_workers=3) as ds:
+    with dsea.Dataset(n, m * 4, o_in=1, o_out=1, n_workers=3) as ds:
         ds.register(kernel)
         for j in range(n):
             ds.write(j, u0[j * m:(j + 1) * m])
@@ -74,12 +76,12 @@ def test_kernel_error_stops_the_run():
     def failing(user, j, step, inp, out, nbytes, stream):
         return dsea.ERR_INVALID_ARG if j == 3 else 0
 
-    with dsea.Dataset(n, m * 8, o_in=1, o_out=0, n_workers=2) as ds:
+    with dsea.Dataset(n, m * 4, o_in=1, o_out=0, n_workers=2) as ds:
         ds.register(failing)
         with pytest.raises(dsea.DseaError) as e:
             ds.run(2)
         assert e.value.code == dsea.ERR_INVALID_ARG
-    with dsea.Dataset(n, m * 8) as ds:                    # no kernel registered
+    with dsea.Dataset(n, m * 4) as ds:                    # no kernel registered
         with pytest.raises(dsea.DseaError) as e:
             ds.run(1)
         assert e.value.code == dsea.ERR_STATE

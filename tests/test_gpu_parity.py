@@ -241,3 +241,28 @@ def test_full_67m_box_sampled_atoms():
     # one step later: the sampled atoms' forces at the GPU's new positions
     F1o, _, _ = oracle.forces_subset(r1, box, idx, RC)
     assert rms(F1[idx] - F1o) <= 2e-6 * rms(F1o)
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_large_cells_many_chunks_and_windows(precision):
+    """Cells of ~39 atoms (wide slices, y/z cells just under 4/3 rc): home
+    cells run in two 32-atom chunks and a neighbourhood spans three list
+    windows of the mixed form."""
+    box = np.array([14.9, 9.99, 9.99])
+    g = [np.arange(k) * (L / k) for k, L in zip((13, 9, 9), box)]   # a simple cubic grid, spacing ~1.1
+    pos = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = inputs.jitter(pos, box, 0.05, seed=32)
+    n = len(pos)
+    vel = inputs.maxwell_boltzmann(n, 1.0, seed=33)
+    Fo, Uo, Wo = oracle.forces(pos, box, RC, "cells")
+    with dsea.Box(pos, vel, box, n_slices=3, precision=precision) as b:
+        inf = b.info()
+        per_cell = n / np.prod(inf["cells"])
+        assert per_cell > 32, per_cell
+        Fg = b.forces()
+        e_rms, _ = force_err(Fg, Fo)
+        assert e_rms <= (1e-12 if precision == dsea.FP64 else 2e-6), e_rms
+        if precision == dsea.FP64:
+            ro, _, _, _ = oracle.run(pos, vel, box, steps=30)
+            b.advance(30)
+            assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
