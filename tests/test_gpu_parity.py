@@ -266,3 +266,61 @@ def test_large_cells_many_chunks_and_windows(precision):
             ro, _, _, _ = oracle.run(pos, vel, box, steps=30)
             b.advance(30)
             assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
+
+
+def _sparse_gas(n, box, dmin, seed):
+    """n atoms uniform in the box, no two closer than dmin (minimum image)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = np.zeros((0, 3))
+    while len(pos) < n:
+        p = rng.uniform(0.0, 1.0, 3) * box
+        if len(pos) == 0 or np.sqrt((min_image(pos - p, box) ** 2).sum(1)).min() >= dmin:
+            pos = np.vstack([pos, p])
+    return pos
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+@pytest.mark.parametrize("n", [240, 864])
+def test_sparse_gas_pairs_at_every_angle(precision, n):
+    """About one (four) atoms per cell: pairs reach the cutoff across faces,
+    edges and corners in every direction.  With four, the mixed form prunes
+    its lists to the neighbours near the small box its home atoms span; with
+    one, a home cell's short list is kept whole."""
+    box = np.array([15.6, 15.6, 15.6])                # 6 cells of 2.6 per axis
+    pos = _sparse_gas(n, box, 0.95, seed=41)
+    Fo, Uo, Wo = oracle.forces(pos, box, RC, "brute")
+    with dsea.Box(pos, None, box, precision=precision) as b:
+        assert b.info()["cells"] == [6, 6, 6]
+        Fg = b.forces()
+        ob = b.observables()
+    tol = 1e-12 if precision == dsea.FP64 else 2e-6
+    e_rms, _ = force_err(Fg, Fo)
+    assert e_rms <= tol, e_rms
+    scale = tol * len(pos) * rms(Fo)                  # U and W are sums of cancelling pair terms
+    assert abs(ob["U"] - Uo) <= scale and abs(ob["W"] - Wo) <= scale
+
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+def test_corner_and_edge_neighbours_near_the_cutoff(precision):
+    """Lone atoms near a cell corner with partners in the corner, edge and
+    face neighbour cells just inside (2.49) and just outside (2.51) the
+    cutoff: the inside pairs interact, the outside ones do not."""
+    box = np.array([10.4, 10.4, 10.4])                 # 4 cells of 2.6 per axis
+    a = np.array([2.55, 2.55, 2.55])                   # near the corner (2.6, 2.6, 2.6) of cell (0, 0, 0)
+    u = [np.array(v, float) / np.linalg.norm(v) for v in ((1, 1, 1), (1, 1, 0), (1, 0, 0))]
+    for d, interacting in ((2.49, True), (2.51, False)):
+        for k in u:
+            pos = np.array([a, a + d * k])
+            Fo, Uo, _ = oracle.forces(pos, box, RC, "brute")
+            assert (Uo != 0.0) == interacting
+            with dsea.Box(pos, None, box, precision=precision) as b:
+                Fg = b.forces()
+                Ug = b.observables()["U"]
+            if interacting:
+                tol = 1e-12 if precision == dsea.FP64 else 2e-6
+                assert np.abs(Fg - Fo).max() <= tol * np.abs(Fo).max()
+                # near the cutoff the shifted pair energy is a small difference
+                # of terms of size 4 r^-6: rounding is relative to those
+                assert abs(Ug - Uo) <= 10 * tol * 4.0 * d ** -6
+            else:
+                assert np.all(Fg == 0.0) and Ug == 0.0
