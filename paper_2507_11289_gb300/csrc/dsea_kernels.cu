@@ -1025,9 +1025,9 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
 // Forces on home atoms [ib, ib + nin) of the warp's home cell from the whole
 // neighbourhood (all windows), packed FP32x2: each lane carries two home
 // atoms (splatted) and meets one entry pair of the list per trip; the ns lane
-// groups split each window's pairs into equal contiguous shares (the home
-// segment, which holds the atoms themselves, by stride with the exact cutoff
-// test).  The partial sums are combined in a fixed order (halves, then
+// groups take each window's pairs by stride (group g every ns-th pair from
+// g; the home segment, which holds the atoms themselves, with the exact
+// cutoff test).  The partial sums are combined in a fixed order (halves, then
 // groups), so each atom's force is summed in an order fixed by the box
 // state.  Lane l < nin returns the totals of home atom ib + l.
 template <bool OBS>
@@ -1072,12 +1072,13 @@ __device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int i
                 pair2<true, OBS>(X0, Y0, Z0, XJ, YJ, ZJ, rc2f, rcb, ush, a0);
                 pair2<true, OBS>(X1, Y1, Z1, XJ, YJ, ZJ, rc2f, rcb, ush, a1);
             }
-            const int M = wp - hp;
-            const int chunk = qdiv(M + ns - 1, inv_of(ns));
-            const float4 *lp = L + 2 * (hp + g * chunk);
-            const float4 *le = L + 2 * (hp + min(M, g * chunk + chunk));
+            // group g takes pairs hp + g, hp + g + ns, ...: at most four groups read
+            // distinct bank quarters in every trip
+            const float4 *lp = L + 2 * (hp + g);
+            const float4 *le = L + 2 * wp;
+            const int stride = 2 * ns;
             DSEA_UNROLL(DSEA_PAIR_UNROLL_N)
-            for (; lp < le; lp += 2) {
+            for (; lp < le; lp += stride) {
                 const float4 xy = lp[0];
                 const float2 ZJ = *reinterpret_cast<const float2 *>(lp + 1);
                 const float2 XJ = make_float2(xy.x, xy.y), YJ = make_float2(xy.z, xy.w);
