@@ -228,13 +228,21 @@ def dataset_run(dsea, torch, stream, n_slices=43, points_per_slice=1 << 23, work
 
 
 def e2e_run(dsea, torch, spec, precision, steps, md_steps, stream):
-    """End to end through the C ABI: host pos/vel in, create + bin on the
-    device, advance, read positions and velocities back to host arrays."""
+    """End to end through the C ABI: host pos/vel in (pinned), create + bin
+    on the device, advance, read positions and velocities back to pinned host
+    arrays."""
     pos, vel, box = spec.state()
-    pos_h = np.ascontiguousarray(pos)
-    vel_h = np.ascontiguousarray(vel)
-    out_r = np.empty_like(pos_h)
-    out_v = np.empty_like(vel_h)
+
+    def pinned(shape):   # page-locked host array (NumPy view of a pinned tensor)
+        t = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        return t, t.numpy()
+
+    keep = []
+    for a in (pos, vel, pos, vel):
+        keep.append(pinned(a.shape))
+    pos_h, vel_h, out_r, out_v = (k[1] for k in keep)
+    pos_h[...] = pos
+    vel_h[...] = vel
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):

@@ -127,7 +127,8 @@ typedef struct {
     int cell_capacity;
     int precision, schedule;
     int64_t n_atoms, step;
-    size_t device_bytes;
+    size_t device_bytes; /* device memory the box holds now (also before registration:
+                            its copy of the initial state) */
     double cell_edge[3];
     int boundary_x;
 } dsea_box_info;
@@ -137,17 +138,25 @@ typedef struct {
 /* Create a box from host positions and velocities (Sec. 3, "the user
  * provides slices of the dataset"; Sec. 4 geometry).  The box is cut into
  * n_slices slices along x of width Lx / n_slices >= rc and into cells of edge
- * >= rc; needs >= 3 slices and >= 3 cells per axis.  Device state is
- * allocated by dsea_register_kernel.  `cuda_stream` is a cudaStream_t (NULL =
- * the legacy default stream).  *out receives the handle. */
+ * >= rc; needs >= 3 slices and >= 3 cells per axis (checked by
+ * dsea_register_kernel, which knows rc).  The positions and velocities are
+ * copied to device buffers owned by the box (through `allocator`) and the
+ * positions checked there; the call returns once the copies are complete, so
+ * the caller may reuse its arrays at once (pinned host memory makes the
+ * copies faster).  Errors: DSEA_ERR_INVALID_ARG for a bad box, boundary code,
+ * an x outside [0, Lx) with mirror walls (all checked before any device
+ * call) or a non-finite position; DSEA_ERR_NO_DEVICE, DSEA_ERR_OOM,
+ * DSEA_ERR_CUDA.  The cell state itself is allocated by
+ * dsea_register_kernel.  `cuda_stream` is a cudaStream_t (NULL = the legacy
+ * default stream).  *out receives the handle. */
 int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator,
                     void *cuda_stream, dsea_box **out);
 
 /* Register the per-slice kernel (Sec. 3.3: the user kernel with input and
  * output order).  kind must be DSEA_KERNEL_LJ_TS and o_in = o_out = 1
  * (Sec. 4); params may be NULL for rc 2.5, dt 0.005, FP64, ring schedule.
- * Allocates the slice/cell state on the device, bins the atoms and makes
- * the box ready to advance. */
+ * Allocates the slice/cell state on the device, bins the atoms, releases
+ * the box's copy of the initial state and makes the box ready to advance. */
 int dsea_register_kernel(dsea_box *box, int kind, int o_in, int o_out, const dsea_params *params);
 
 /* Advance n_steps >= 0 velocity-Verlet steps (Algorithm 1), asynchronously

@@ -62,20 +62,58 @@ void *dev_alloc(dsea_box *b, size_t bytes)
         p = nullptr;
     }
     if (p) {
-        b->allocs.push_back(p);
+        b->allocs.emplace_back(p, bytes);
         b->device_bytes += bytes;
     }
     return p;
 }
 
+void dev_release(dsea_box *b, void *p)
+{
+    if (b->has_alloc) b->alloc.free(p, b->alloc.ctx);
+    else cudaFree(p);
+}
+
+// Free one allocation of the box before the box itself goes.
+void dev_free(dsea_box *b, void *p)
+{
+    for (size_t k = 0; k < b->allocs.size(); ++k) {
+        if (b->allocs[k].first != p) continue;
+        dev_release(b, p);
+        b->device_bytes -= b->allocs[k].second;
+        b->allocs.erase(b->allocs.begin() + (long)k);
+        return;
+    }
+}
+
 void dev_free_all(dsea_box *b)
 {
-    for (void *p : b->allocs) {
-        if (b->has_alloc) b->alloc.free(p, b->alloc.ctx);
-        else cudaFree(p);
-    }
+    for (auto &a : b->allocs) dev_release(b, a.first);
     b->allocs.clear();
     b->device_bytes = 0;
+}
+
+// Copy the caller's positions (and velocities) into device buffers of the
+// box and check that they are finite; waits for the copies, so the caller may
+// reuse its arrays as soon as dsea_box_create returns.
+int upload_initial_state(dsea_box *b, const dsea_box_desc *desc)
+{
+    const long long n3 = 3LL * desc->n_atoms;
+    if (n3 == 0) return DSEA_OK;
+    const size_t nb = sizeof(double) * (size_t)n3;
+    b->d_pos0 = (double *)dev_alloc(b, nb);
+    if (b->has_vel) b->d_vel0 = (double *)dev_alloc(b, nb);
+    int *d_flag = (int *)dev_alloc(b, sizeof(int));
+    if (!b->d_pos0 || (b->has_vel && !b->d_vel0) || !d_flag) return DSEA_ERR_OOM;
+    CU(cudaMemsetAsync(d_flag, 0, sizeof(int), b->stream));
+    CU(cudaMemcpyAsync(b->d_pos0, desc->pos, nb, cudaMemcpyHostToDevice, b->stream));
+    if (b->has_vel) CU(cudaMemcpyAsync(b->d_vel0, desc->vel, nb, cudaMemcpyHostToDevice, b->stream));
+    CU(dsea::launch_check_finite(b->d_pos0, n3, d_flag, b->stream));
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    dev_free(b, d_flag);
+    return flag ? DSEA_ERR_INVALID_ARG : DSEA_OK;
 }
 
 int num_sms()
@@ -384,14 +422,14 @@ int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, 
     b->walls_x = desc->boundary_x == DSEA_BOUNDARY_MIRROR ? 1 : 0;
     for (int d = 0; d < 3; ++d) b->L[d] = desc->box[d];
     b->hb.n_atoms = desc->n_atoms;
-    b->pos0.assign(desc->pos, desc->pos + 3 * desc->n_atoms);
     b->has_vel = desc->vel != nullptr;
-    if (b->has_vel) b->vel0.assign(desc->vel, desc->vel + 3 * desc->n_atoms);
-    for (double x : b->pos0)
-        if (!std::isfinite(x)) {
-            delete b;
-            return DSEA_ERR_INVALID_ARG;
-        }
+    const int rc = upload_initial_state(b, desc);
+    if (rc) {
+        cudaStreamSynchronize(b->stream);
+        dev_free_all(b);
+        delete b;
+        return rc;
+    }
     *out = b;
     return DSEA_OK;
 }
@@ -457,32 +495,15 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
         CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * 2 * hb.n_cells, b->stream));
     }
     CU(cudaMemsetAsync(hb.err, 0, sizeof(int), b->stream));
-    // bin the initial atoms into the buffer of step 0
-    double *d_pos = nullptr, *d_vel = nullptr;
-    const size_t nb = sizeof(double) * 3 * (size_t)std::max<int64_t>(hb.n_atoms, 1);
-    CU(cudaMalloc(&d_pos, nb));
-    if (b->has_vel && cudaMalloc(&d_vel, nb) != cudaSuccess) {
-        cudaFree(d_pos);
-        return DSEA_ERR_OOM;
-    }
-    int rc = DSEA_OK;
-    if (hb.n_atoms > 0) {
-        cudaMemcpyAsync(d_pos, b->pos0.data(), sizeof(double) * 3 * hb.n_atoms, cudaMemcpyHostToDevice,
-                        b->stream);
-        if (d_vel)
-            cudaMemcpyAsync(d_vel, b->vel0.data(), sizeof(double) * 3 * hb.n_atoms,
-                            cudaMemcpyHostToDevice, b->stream);
-    }
-    rc = upload_desc(b);
-    if (!rc) rc = map_cuda(dsea::launch_bin(hb, b->db, d_pos, d_vel, b->stream));
+    // bin the initial atoms (copied to the device by dsea_box_create) into the
+    // buffer of step 0, then release those copies
+    int rc = upload_desc(b);
+    if (!rc) rc = map_cuda(dsea::launch_bin(hb, b->db, b->d_pos0, b->d_vel0, b->stream));
     if (!rc) rc = check_device_error(b);
-    cudaFree(d_pos);
-    if (d_vel) cudaFree(d_vel);
     if (rc) return rc;
-    b->pos0.clear();
-    b->pos0.shrink_to_fit();
-    b->vel0.clear();
-    b->vel0.shrink_to_fit();
+    if (b->d_pos0) dev_free(b, b->d_pos0);
+    if (b->d_vel0) dev_free(b, b->d_vel0);
+    b->d_pos0 = b->d_vel0 = nullptr;
     b->registered = true;
     return DSEA_OK;
 }
@@ -578,6 +599,7 @@ int dsea_box_get_info(const dsea_box *b, dsea_box_info *o)
     o->n_atoms = hb.n_atoms;
     o->step = hb.step;
     o->boundary_x = b->walls_x ? DSEA_BOUNDARY_MIRROR : DSEA_BOUNDARY_PERIODIC;
+    o->device_bytes = b->device_bytes;
     if (!b->registered) return DSEA_OK;
     o->n_slices = hb.n_slices;
     o->cells_per_slice_x = hb.cps;
@@ -591,7 +613,6 @@ int dsea_box_get_info(const dsea_box *b, dsea_box_info *o)
     o->cell_capacity = hb.cap;
     o->precision = hb.precision;
     o->schedule = b->params.schedule;
-    o->device_bytes = b->device_bytes;
     return DSEA_OK;
 }
 

@@ -6,6 +6,7 @@
 #include "dsea_internal.h"
 
 #include <map>
+#include <utility>
 #include <vector>
 
 struct dsea_box {
@@ -16,14 +17,15 @@ struct dsea_box {
     int n_slices_req = 0;
     double L[3] = {0, 0, 0};
     int walls_x = 0;                  // DSEA_BOUNDARY_MIRROR along x
-    std::vector<double> pos0, vel0;   // host copies until the kernel is registered
+    double *d_pos0 = nullptr;         // device copies of the caller's positions and
+    double *d_vel0 = nullptr;         // velocities until the kernel is registered
     bool has_vel = false;
     bool registered = false;
     dsea_params params{};
     double mean_cap = 0;              // expected atoms per cell used for stage sizing
     dsea::BoxDev hb{};
     dsea::BoxDev *db = nullptr;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // live device allocations and their sizes
     size_t device_bytes = 0;
     // ring plan buffers of single-box launches
     int64_t *d_step_base = nullptr;

@@ -89,6 +89,8 @@ size_t unit_smem_bytes(int precision, int staged_cells, int smem_atoms);
 size_t max_unit_smem_bytes();
 
 // Bin atoms (device AoS pos/vel, atom-ID order) into the buffer of `box.step`.
+// flag = 1 if any of a[0..n) is not finite (flag is left alone otherwise).
+cudaError_t launch_check_finite(const double *a, long long n, int *flag, cudaStream_t stream);
 cudaError_t launch_bin(const BoxDev &host_box, const BoxDev *dev_box, const double *pos,
                        const double *vel, cudaStream_t stream);
 

@@ -1673,6 +1673,22 @@ size_t max_unit_smem_bytes()
     return (size_t)v > 4096 ? (size_t)v - 4096 : 0;
 }
 
+__global__ void __launch_bounds__(256) k_check_finite(const double *a, long long n, int *flag)
+{
+    bool bad = false;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        bad |= !isfinite(a[i]);
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+cudaError_t launch_check_finite(const double *a, long long n, int *flag, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = (n + 255) / 256;
+    k_check_finite<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const BoxDev &hb, const BoxDev *db, const double *pos, const double *vel,
                        cudaStream_t stream)
 {

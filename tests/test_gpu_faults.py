@@ -69,3 +69,41 @@ def test_invalid_calls():
             dsea.register_kernel(h, kind=2)
     finally:
         dsea.box_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_non_finite_positions_are_rejected_at_create(bad):
+    """dsea_box_create copies the caller's arrays to the device and checks
+    them there before it returns."""
+    pos, vel, box = inputs.SMALL_4K.state()
+    pos = pos.copy()
+    pos[1234, 2] = bad
+    with pytest.raises(dsea.DseaError) as e:
+        dsea.box_create(pos, vel, box, 4)
+    assert e.value.code == dsea.ERR_INVALID_ARG
+    _still_usable()
+
+
+def test_caller_arrays_may_change_after_create():
+    """The box owns its device copy of the initial state once create returns:
+    the caller's arrays can be overwritten before registration, and the copy
+    is released once the atoms are binned."""
+    pos, vel, box = inputs.SMALL_4K.state()
+    p, v = pos.copy(), vel.copy()
+    n = len(pos)
+    h = dsea.box_create(p, v, box, 4)
+    h0 = dsea.box_create(p, None, box, 4)           # no velocities: no velocity copy
+    try:
+        assert dsea.box_get_info(h)["device_bytes"] == 2 * 24 * n
+        assert dsea.box_get_info(h0)["device_bytes"] == 24 * n
+        p[:] = 0.5
+        v[:] = 7.0
+        for x in (h, h0):
+            dsea.register_kernel(x, dsea.make_params(precision=dsea.FP64))
+        assert np.array_equal(dsea.read_positions(h), pos)
+        assert np.array_equal(dsea.read_velocities(h), vel)
+        assert np.all(dsea.read_velocities(h0) == 0.0)
+        assert dsea.box_get_info(h)["device_bytes"] == dsea.box_get_info(h0)["device_bytes"]
+    finally:
+        dsea.box_destroy(h)
+        dsea.box_destroy(h0)
