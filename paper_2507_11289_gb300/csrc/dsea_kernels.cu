@@ -204,6 +204,47 @@ __device__ __forceinline__ float le_mask(float a, float b)
     return d;
 }
 
+// Neighbour pruning (both forms): a candidate farther than the cutoff from
+// the bounding box of the home atoms a warp evaluates is out of range of all
+// of them.  The test runs in FP32 with these margins, far above its rounding.
+constexpr float kFarAway = 1.0e4f;            // coordinate of a padding entry (never within the cutoff)
+constexpr float kBoxMargin = 1.0e-4f;         // widening of the home atoms' bounding box
+constexpr float kReachMargin = 1.0e-3f;       // widening of rc^2
+
+// A signed integer that orders as the float f does (finite f; -0 just
+// below +0), and back: positive floats order as their bit patterns, negative
+// ones in reverse, so the magnitude bits of negatives are flipped.
+__device__ __forceinline__ int ordered_int(float f)
+{
+    const int i = __float_as_int(f);
+    return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float ordered_float(int i)
+{
+    return __int_as_float(i ^ ((i >> 31) & 0x7fffffff));
+}
+
+// Squared distance from (x, y, z) to the box [lo, hi] (0 inside).
+__device__ __forceinline__ float box_dist2(float x, float y, float z, const float lo[3], const float hi[3])
+{
+    const float dx = fmaxf(fmaxf(lo[0] - x, x - hi[0]), 0.f);
+    const float dy = fmaxf(fmaxf(lo[1] - y, y - hi[1]), 0.f);
+    const float dz = fmaxf(fmaxf(lo[2] - z, z - hi[2]), 0.f);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Warp-wide bounding box of the points held by lanes with `own` set (empty:
+// lo > hi), widened by kBoxMargin.
+__device__ __forceinline__ void warp_box(bool own, float x, float y, float z, float lo[3], float hi[3])
+{
+    const float c[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = ordered_float(__reduce_min_sync(kFull, ordered_int(own ? c[d] : kFarAway))) - kBoxMargin;
+        hi[d] = ordered_float(__reduce_max_sync(kFull, ordered_int(own ? c[d] : -kFarAway))) + kBoxMargin;
+    }
+}
+
 // Accumulators of the two home atoms a lane carries (packed halves).
 struct Acc2 {
     float2 fx, fy, fz, u, w;
@@ -610,18 +651,68 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             long long slot = 0;
             if (own) slot = s_slot[is];
             Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
-            if (act) {
-                const double xi = s_x[is], yi = s_y[is], zi = s_z[is];
-                for (int ox = -1; ox <= 1; ++ox)
-                    for (int oy = -1; oy <= 1; ++oy)
-                        for (int oz = -1; oz <= 1; ++oz) {
-                            const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
-                            const int cs = s_start[kn], cn = s_cnt[kn];
-                            for (int t = g; t < cn; t += ns)
-                                pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t], B.rc2,
-                                              B.ushift, a64);
-                        }
+            // The warp's scratch (32 x 5 doubles) holds, during the pair loop, the
+            // pruned list of one neighbour cell (ints 0..127) and the chunk's
+            // bounding box in FP32 relative to its first atom (box at float 192,
+            // reference atom at double 104), re-read per cell to spare registers.
+            int *plist = reinterpret_cast<int *>(smem + Ly.scr) + warp * 32 * 10;
+            float *s_box = reinterpret_cast<float *>(plist) + 192;
+            double *s_ref = reinterpret_cast<double *>(plist) + 104;
+            {
+                const double xr = s_x[hs + ib], yr = s_y[hs + ib], zr = s_z[hs + ib];
+                const int ih = hs + ib + (own ? lane : 0);
+                float lo[3], hi[3];
+                warp_box(own, (float)(s_x[ih] - xr), (float)(s_y[ih] - yr), (float)(s_z[ih] - zr), lo, hi);
+                if (lane == 0) {
+                    for (int d = 0; d < 3; ++d) {
+                        s_box[d] = lo[d];
+                        s_box[3 + d] = hi[d];
+                    }
+                    s_ref[0] = xr;
+                    s_ref[1] = yr;
+                    s_ref[2] = zr;
+                }
+                __syncwarp();
             }
+            const double xi = act ? s_x[is] : 0.0, yi = act ? s_y[is] : 0.0, zi = act ? s_z[is] : 0.0;
+            for (int ox = -1; ox <= 1; ++ox)
+                for (int oy = -1; oy <= 1; ++oy)
+                    for (int oz = -1; oz <= 1; ++oz) {
+                        const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
+                        const int cs = s_start[kn], cn = s_cnt[kn];
+                        if (kn == kh) {   // the home cell: every atom
+                            if (act)
+                                for (int t = g; t < cn; t += ns)
+                                    pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t], B.rc2,
+                                                  B.ushift, a64);
+                            continue;
+                        }
+                        // the cell's atoms within the cutoff of the box, in order (at most
+                        // cap <= 128 of them); the others would all fail the cutoff test
+                        int m = 0;
+                        for (int t0 = 0; t0 < cn; t0 += 32) {
+                            const int t = t0 + lane;
+                            bool keep = false;
+                            if (t < cn) {
+                                const volatile float *vb = s_box;
+                                const volatile double *vr = s_ref;
+                                const float lo[3] = {vb[0], vb[1], vb[2]}, hi[3] = {vb[3], vb[4], vb[5]};
+                                keep = box_dist2((float)(s_x[cs + t] - vr[0]), (float)(s_y[cs + t] - vr[1]),
+                                                 (float)(s_z[cs + t] - vr[2]), lo, hi) <=
+                                       B.rc2f + kReachMargin;
+                            }
+                            const unsigned kept = __ballot_sync(kFull, keep);
+                            if (keep) plist[m + __popc(kept & ((1u << lane) - 1u))] = cs + t;
+                            m += __popc(kept);
+                        }
+                        __syncwarp();
+                        if (act)
+                            for (int e = g; e < m; e += ns) {
+                                const int q = plist[e];
+                                pair_f64<OBS>(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.rc2, B.ushift, a64);
+                            }
+                        __syncwarp();
+                    }
             // combine the ns partial sums of each home atom in split order
             double fx = a64.fx, fy = a64.fy, fz = a64.fz, uu = a64.u, ww = a64.w;
             if (ns > 1) {
@@ -790,9 +881,6 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
 #endif
 constexpr int kListAtoms = DSEA_LIST_ATOMS;   // list window (entries, even) of one warp
 constexpr int kHomeMax = 128;                 // largest cell capacity (slots of one home cell)
-constexpr float kFarAway = 1.0e4f;            // coordinate of a padding entry (never within the cutoff)
-constexpr float kBoxMargin = 1.0e-4f;         // widening of the home atoms' bounding box for the pruning test
-constexpr float kReachMargin = 1.0e-3f;       // widening of rc^2 for the pruning test
 
 // Per-warp shared memory of the mixed form.  The context fields are written
 // once per home cell and read back through volatile loads where they are
@@ -817,19 +905,6 @@ struct WarpArea {
 struct ObsAcc {
     double u, w, k, n;
 };
-
-// A signed integer that orders as the float f does (finite f; -0 just
-// below +0), and back: positive floats order as their bit patterns, negative
-// ones in reverse, so the magnitude bits of negatives are flipped.
-__device__ __forceinline__ int ordered_int(float f)
-{
-    const int i = __float_as_int(f);
-    return i ^ ((i >> 31) & 0x7fffffff);
-}
-__device__ __forceinline__ float ordered_float(int i)
-{
-    return __int_as_float(i ^ ((i >> 31) & 0x7fffffff));
-}
 
 // Entry e of the list window: its x (y, z and the id bits follow at +2,
 // +4 and +6 floats).
@@ -998,10 +1073,7 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         bool keep = false;
         if (e < n_raw) {
             a = raw[e];
-            const float dx = fmaxf(fmaxf(lo[0] - a.x, a.x - hi[0]), 0.f),
-                        dy = fmaxf(fmaxf(lo[1] - a.y, a.y - hi[1]), 0.f),
-                        dz = fmaxf(fmaxf(lo[2] - a.z, a.z - hi[2]), 0.f);
-            keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= reach2;
+            keep = box_dist2(a.x, a.y, a.z, lo, hi) <= reach2;
         }
         const unsigned kept = __ballot_sync(kFull, keep);
         __syncwarp();
