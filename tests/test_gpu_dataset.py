@@ -28,9 +28,10 @@ def rod(n_slices, m, seed=11):
     return rng.uniform(-1.0, 1.0, n_slices * m).astype(np.float32)
 
 
-@pytest.mark.parametrize("workers", [1, 2, 3])
-def test_heat_ring_equals_numpy_bitwise(workers):
-    n, m, a = 7, 1000, 0.23
+@pytest.mark.parametrize("workers,m", [(1, 1000), (2, 1000), (3, 1000), (2, 1001)])
+def test_heat_ring_equals_numpy_bitwise(workers, m):
+    """m = 1000: the kernel's four-point path; m = 1001: its one-point path."""
+    n, a = 7, 0.23
     u0 = rod(n, m)
     with dsea.Dataset(n, m * 4, o_in=1, o_out=0, n_workers=workers) as ds:
         ds.register("heat1d", a)
