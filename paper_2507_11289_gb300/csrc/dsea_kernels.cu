@@ -1165,16 +1165,26 @@ __device__ __forceinline__ void home_forces(const BoxDev &B, WarpArea &wa, int i
     const float2 FZ = make_float2(a0.fz.x + a0.fz.y, a1.fz.x + a1.fz.y);
     const float2 UU = make_float2(a0.u.x + a0.u.y, a1.u.x + a1.u.y);
     const float2 WW = make_float2(a0.w.x + a0.w.y, a1.w.x + a1.w.y);
-    // combine the ns partials of each atom pair into lane pi, in group order
+    // combine the ns partials of each atom pair into lane pi (group 0) by a
+    // fixed tree over the groups: at distance d, group g (a multiple of 2d)
+    // adds group g + d when it exists; at most five levels
     float2 SX = FX, SY = FY, SZ = FZ, SU = UU, SW = WW;
-    for (int gg = 1; gg < ns; ++gg) {
-        const int src = pi + gg * np;   // < ns * np <= 32
-        SX.x += __shfl_sync(kFull, FX.x, src); SX.y += __shfl_sync(kFull, FX.y, src);
-        SY.x += __shfl_sync(kFull, FY.x, src); SY.y += __shfl_sync(kFull, FY.y, src);
-        SZ.x += __shfl_sync(kFull, FZ.x, src); SZ.y += __shfl_sync(kFull, FZ.y, src);
+#pragma unroll 1
+    for (int d = 1; d < ns; d <<= 1) {
+        const int off = d * np;   // lane + off < ns * np <= 32 whenever it is added
+        const bool add = (g & (2 * d - 1)) == 0 && g + d < ns;
+        float t;
+        t = __shfl_down_sync(kFull, SX.x, off); if (add) SX.x += t;
+        t = __shfl_down_sync(kFull, SX.y, off); if (add) SX.y += t;
+        t = __shfl_down_sync(kFull, SY.x, off); if (add) SY.x += t;
+        t = __shfl_down_sync(kFull, SY.y, off); if (add) SY.y += t;
+        t = __shfl_down_sync(kFull, SZ.x, off); if (add) SZ.x += t;
+        t = __shfl_down_sync(kFull, SZ.y, off); if (add) SZ.y += t;
         if (OBS) {
-            SU.x += __shfl_sync(kFull, UU.x, src); SU.y += __shfl_sync(kFull, UU.y, src);
-            SW.x += __shfl_sync(kFull, WW.x, src); SW.y += __shfl_sync(kFull, WW.y, src);
+            t = __shfl_down_sync(kFull, SU.x, off); if (add) SU.x += t;
+            t = __shfl_down_sync(kFull, SU.y, off); if (add) SU.y += t;
+            t = __shfl_down_sync(kFull, SW.x, off); if (add) SW.x += t;
+            t = __shfl_down_sync(kFull, SW.y, off); if (add) SW.y += t;
         }
     }
     // atom l (l < nin) is half l & 1 of the pair held by lane l >> 1
