@@ -259,20 +259,27 @@ int read_array(dsea_box *b, double *out, int64_t n)
 }
 
 struct TuneKey {
-    int nc0, nc1, nc2, cps, cap, precision;
+    int occ, size, nc1, nc2, cps, cap, precision;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(nc0, nc1, nc2, cps, cap, precision) <
-               std::tie(o.nc0, o.nc1, o.nc2, o.cps, o.cap, o.precision);
+        return std::tie(occ, size, nc1, nc2, cps, cap, precision) <
+               std::tie(o.occ, o.size, o.nc1, o.nc2, o.cps, o.cap, o.precision);
     }
 };
-// Size class of the autotuner cache: the unit shape depends on the cells per
-// axis in the unit plane (up to 16, beyond which boxes behave alike), the
-// cell layers per slice, the cell capacity (a proxy for atoms per cell) and
-// the precision; the number of slices does not change the best shape.
-TuneKey size_class(const int *nc, int cps, int cap, int precision)
+// Size class of the autotuner cache.  The best unit shape depends on
+// - the total number of cells (in octaves): smaller units give a small box
+//   enough units to fill the GPU, larger ones save per-unit work in a big box;
+// - the mean atoms per cell (in half-octaves): per-cell costs dominate dilute
+//   boxes, pair work dense ones;
+// - the cells per axis in the unit plane (up to 16: the edge units' share);
+// - the cell layers per slice, the cell capacity and the precision.
+TuneKey size_class(const int *nc, int cps, int cap, int precision, int64_t n_atoms)
 {
-    return TuneKey{0, std::min(nc[1], 16), std::min(nc[2], 16), cps, cap, precision};
+    const double cells = (double)nc[0] * nc[1] * nc[2];
+    const double mean = cells > 0 ? (double)n_atoms / cells : 0.0;
+    const int occ = (int)std::floor(2.0 * std::log2(mean + 1.0));
+    const int size = (int)std::floor(std::log2(std::max(cells, 1.0)));
+    return TuneKey{occ, size, std::min(nc[1], 16), std::min(nc[2], 16), cps, cap, precision};
 }
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
@@ -343,7 +350,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     int ty = p.tile_y, tz = p.tile_z;
     if (ty == 0 || tz == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(size_class(hb.nc, cps, cap, p.precision));
+        auto it = g_tune_cache.find(size_class(hb.nc, cps, cap, p.precision, n_atoms));
         if (it != g_tune_cache.end()) {
             ty = it->second.first;
             tz = it->second.second;
@@ -747,7 +754,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
     int rc = check_device_error(b);
     if (rc) return rc;
     BoxDev &hb = b->hb;
-    const TuneKey key = size_class(hb.nc, hb.cps, hb.cap, hb.precision);
+    const TuneKey key = size_class(hb.nc, hb.cps, hb.cap, hb.precision, hb.n_atoms);
     std::pair<int, int> best{hb.tile_y, hb.tile_z};
     bool cached = false;
     {

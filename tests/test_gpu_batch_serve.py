@@ -123,3 +123,41 @@ def test_torch_allocator_owns_box_memory():
     assert during - before >= b.info()["device_bytes"] * 0.9
     b.close()
     assert torch.cuda.memory_allocated() == before
+
+
+def test_autotune_choice_does_not_leak_across_densities():
+    """The autotuner caches a unit shape per size class.  A dilute box and a
+    dense one with the same cells per axis and the same cell capacity are
+    different classes (mean atoms per cell), and so are a 17^3-cell box and
+    the 43^3-cell 1M-atom box at the same density (total cells): tuning the
+    first of each pair leaves the second on the default shape.  Run in a
+    fresh process: the cache lives as long as the library."""
+    import subprocess
+    import sys
+    code = """
+import json
+from paper_2507_11289_gb300 import dsea, inputs
+out = {}
+for name, n_i, rho in (("dilute", 10, 0.05), ("dense", 25, 0.8), ("big", 64, 0.8)):
+    pos, box = inputs.fcc_lattice(n_i, rho)
+    vel = inputs.maxwell_boltzmann(len(pos), 1.0, 3)
+    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+        inf = b.info()
+        out[name] = {"cells": inf["cells"], "cap": inf["cell_capacity"],
+                     "tile": [inf["tile_y"], inf["tile_z"]]}
+        if name != "big":
+            p = b.autotune(trial_steps=2)
+            out[name]["tuned"] = [p["tile_y"], p["tile_z"]]
+print(json.dumps(out))
+"""
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    d, e, g = out["dilute"], out["dense"], out["big"]
+    assert d["cells"] == e["cells"] and d["cap"] == e["cap"]       # the same key without density
+    assert e["tile"] == [2, 4], out                                # the mixed default, untouched
+    assert g["cap"] == e["cap"] and min(g["cells"][1:]) >= 16 and min(e["cells"][1:]) >= 16
+    assert g["tile"] == [2, 4], out                                # not the 17^3 box's choice
