@@ -913,13 +913,28 @@ __device__ __forceinline__ float *list_entry(WarpArea &wa, int e)
     return reinterpret_cast<float *>(&wa.list[2 * (e >> 1)]) + (e & 1);
 }
 
+// Unit offsets (ox, oy, oz) of the 27 neighbourhood cells in (ox, oy, oz)
+// order, padded with zeros to 32 rows so that any 5-bit index stays inside;
+// one table per CTA, filled (fill_offsets) by every kernel that builds
+// mixed-form lists before its first list.
+__shared__ float4 g_offsets[32];
+
+__device__ __forceinline__ void fill_offsets()
+{
+    const int k = threadIdx.x;
+    if (k < 32)
+        g_offsets[k] = k < 27 ? make_float4((float)(k / 9 - 1), (float)((k / 3) % 3 - 1), (float)(k % 3 - 1), 0.f)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+}
+
 // Lane c (< 27) of a warp describes one cell of the neighbourhood of home
 // cell (hx, hy, hz): lane 0 the home cell, lanes 1..26 the others.
 struct NbrCell {
     int gc;           // global cell index
     int n_s, n_a;     // stayers (front slots) and arrivals (back slots)
     int pre;          // first list entry of the cell
-    float sx, sy, sz; // shift of the cell's centre from the home cell's centre
+    int kk;           // index of the cell's offset in g_offsets (13: the home cell)
 };
 
 // The neighbourhood of a home cell; `total` receives the list length, padded
@@ -927,7 +942,7 @@ struct NbrCell {
 __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag, int hx, int hy, int hz,
                                             int lane, int &total)
 {
-    NbrCell c = {0, 0, 0, 0, 0.f, 0.f, 0.f};
+    NbrCell c = {0, 0, 0, 0, 13};
     const int kk = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);
     const int ox = kk / 9 - 1;
     if (lane < 27 && !(B.walls_x && (hx + ox < 0 || hx + ox >= B.nc[0]))) {   // nothing beyond a wall
@@ -946,9 +961,7 @@ __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag
         c.gc = gc;
         c.n_s = n_s;
         c.n_a = n_a;
-        c.sx = (float)ox * B.lcf[0];
-        c.sy = (float)oy * B.lcf[1];
-        c.sz = (float)oz * B.lcf[2];
+        c.kk = kk;
     }
     const int n = c.n_s + c.n_a;
     const int nl = lane == 0 ? (n + 1) & ~1 : n;   // the home segment ends on a pair boundary
@@ -968,11 +981,15 @@ __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag
 // its stayers in slot order, then its arrivals ordered by atom id.  Home
 // cell entries also record their slot.  Padding entries sit far away.  The
 // stayers arrive by asynchronous 16-byte copies (all of a cell's in flight at
-// once) as whole entries; each lane then shifts its cell's entries into the
-// home frame, and one warp-wide pass drops the entries beyond the cutoff of
-// the home atoms' bounding box and writes the rest, in order, into the
+// once) as whole entries; each lane then tags its cell's entries with the
+// cell's offset index (in w, whose atom id is not needed for a neighbour),
+// and one warp-wide pass shifts every entry into the home frame by its
+// tag's offset, drops the entries beyond the cutoff of the home atoms'
+// bounding box and writes the rest, in order, into the
 // [x0 x1 y0 y1 | z0 z1 w0 w1] pair layout in place.  wa.wlen receives the
-// window's entry count after that pass.
+// window's entry count after that pass.  (A per-lane shift pass over each
+// cell's entries cost more shared-memory wavefronts: its lanes touch
+// scattered 16-byte entries.)
 __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCell &c, int total, int w0,
                                              int lane, WarpArea &wa)
 {
@@ -1013,12 +1030,9 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         if (lane == 26 && c.pre + c.n_s + c.n_a < total && total - 1 >= w0 && total - 1 < w1)
             raw[total - 1 - w0] = make_float4(kFarAway, kFarAway, kFarAway, 0.f);
         cp_async_wait_all();
-        if (lane > 0) {   // into the home cell's frame
+        if (lane > 0) {   // tag each entry with its cell's offset (the id is not needed any more)
             const int e0 = max(c.pre, w0), e1 = min(c.pre + c.n_s + c.n_a, w1);
-            for (int e = e0; e < e1; ++e) {
-                const float4 a = raw[e - w0];
-                raw[e - w0] = make_float4(a.x + c.sx, a.y + c.sy, a.z + c.sz, a.w);
-            }
+            for (int e = e0; e < e1; ++e) reinterpret_cast<int *>(&raw[e - w0])[3] = c.kk;
         }
     }
     __syncwarp();
@@ -1073,6 +1087,13 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         bool keep = false;
         if (e < n_raw) {
             a = raw[e];
+            // into the home cell's frame: the same FP32 sum as shifting by ox lc
+            // (ox lc is exact); a padding entry (tag 0) stays far away
+            const float4 o = g_offsets[__float_as_int(a.w) & 31];
+            const volatile float *lc = B.lcf;
+            a.x = fmaf(o.x, lc[0], a.x);
+            a.y = fmaf(o.y, lc[1], a.y);
+            a.z = fmaf(o.z, lc[2], a.z);
             keep = box_dist2(a.x, a.y, a.z, lo, hi) <= reach2;
         }
         const unsigned kept = __ballot_sync(kFull, keep);
@@ -1470,7 +1491,7 @@ __global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;
     if (threadIdx.x == 0) sB = *bp;
-    __syncthreads();
+    fill_offsets();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int u = blockIdx.x * kWarps + warp;
     if (u >= sB.n_slices * sB.units_per_slice) return;
@@ -1644,7 +1665,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
     BoxDev &B = s_box[warp];
     ObsAcc red = {0.0, 0.0, 0.0, 0.0};   // unused (no reduction in the ring)
     if (lane == 0) wa.box = -1;
-    __syncwarp();
+    fill_offsets();
     while (true) {
         int go = 1;   // 0: stop the warp, 1: run the unit, 2: skip it
         int bl = 0;
