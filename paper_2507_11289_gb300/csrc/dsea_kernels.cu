@@ -363,7 +363,9 @@ __device__ __forceinline__ long long place_slot(const BoxDev &B, int pn, long lo
     const unsigned bs = __ballot_sync(kFull, stay);
     const int k_stay = n_stay + __popc(bs & ((1u << lane) - 1u));
     n_stay += __popc(bs);
-    const int k = reserve_slot(B.arr[pn], dest, own && !stay, tag, lane, B.err);
+    // most chunks have no atom that changes cell: skip the reservation then
+    const int k = __any_sync(kFull, own && !stay) ? reserve_slot(B.arr[pn], dest, own && !stay, tag, lane, B.err)
+                                                  : -1;
     if (!own) return -1;
     if (stay) return hcell * B.cap + k_stay;   // stayers never outnumber the cell's atoms
     if (k >= B.cap) {
