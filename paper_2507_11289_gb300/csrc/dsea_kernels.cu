@@ -1078,8 +1078,8 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
     // rounding margin) of the box, which holds every home atom; a dropped
     // entry is out of range of all of them, so its pair terms would all have
     // been masked to zero.  Kept entries are compacted in order into the
-    // pair layout, in place: an entry never moves up, and a round's writes
-    // land below the next round's reads.
+    // pair layout, in place: an entry never moves up, and each 32-entry
+    // sweep writes below the entries the next sweep reads.
     const float reach2 = B.rc2f + kReachMargin;
     const unsigned below = (1u << lane) - 1u;
     int m = k0;
