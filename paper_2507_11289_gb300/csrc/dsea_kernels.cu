@@ -90,8 +90,11 @@ __device__ __forceinline__ float inv_of(int d)
 
 // Shared-memory carve-up of one FP64 unit.
 struct Layout {
-    size_t cnt, nst, start, gcell, atoms, id, slot, scr, red, cellke, lam, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, id, slot, scr, queue, red, cellke, lam, ctr, total;
 };
+
+// Depth of the per-lane queue of in-range candidates in the FP64 pair loop.
+constexpr int kQueueDepth = 16;
 
 __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
 {
@@ -107,6 +110,7 @@ __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
     L.slot = o;  o += sizeof(int) * smem_atoms;
     o = align16(o);
     L.scr = o;   o += sizeof(double) * kThreads * 5;     // partial sums of split home atoms
+    L.queue = o; o += sizeof(int) * kThreads * kQueueDepth;   // queued in-range candidates
     L.red = o;   o += sizeof(double) * kWarps * 4;
     L.cellke = o; o += sizeof(double) * 2 * staged_cells;   // thermostat: (KE, N) per home cell
     L.lam = o;   o += 16;
@@ -292,25 +296,34 @@ __device__ __forceinline__ void pair2(const float2 XS, const float2 YS, const fl
     }
 }
 
-// One candidate pair in FP64 on absolute (periodically shifted) positions.
+// The force terms of one pair in range, in FP64 on absolute (periodically
+// shifted) positions.
 template <bool OBS>
 __device__ __forceinline__ void pair_f64(double xi, double yi, double zi, double xj, double yj,
-                                         double zj, double rc2, double ushift, Acc64 &a)
+                                         double zj, double ushift, Acc64 &a)
 {
     const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
     const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 <= rc2 && r2 > 0.0) {
-        const double r2i = 1.0 / r2;
-        const double r6i = r2i * r2i * r2i;
-        const double fs = 24.0 * (2.0 * r6i * r6i - r6i) * r2i;
-        a.fx += dx * fs;
-        a.fy += dy * fs;
-        a.fz += dz * fs;
-        if (OBS) {
-            a.u += 4.0 * (r6i * r6i - r6i) + ushift;
-            a.w += r2 * fs;
-        }
+    const double r2i = 1.0 / r2;
+    const double r6i = r2i * r2i * r2i;
+    const double fs = 24.0 * (2.0 * r6i * r6i - r6i) * r2i;
+    a.fx += dx * fs;
+    a.fy += dy * fs;
+    a.fz += dz * fs;
+    if (OBS) {
+        a.u += 4.0 * (r6i * r6i - r6i) + ushift;
+        a.w += r2 * fs;
     }
+}
+
+// Whether a candidate pair counts: within the (inclusive) cutoff and not the
+// atom itself; the same r2 as pair_f64 computes.
+__device__ __forceinline__ bool in_range_f64(double xi, double yi, double zi, double xj, double yj, double zj,
+                                             double rc2)
+{
+    const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    return r2 <= rc2 && r2 > 0.0;
 }
 
 // Reserve one slot per active lane in cell `dest` of the next-step buffer;
@@ -677,16 +690,33 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 __syncwarp();
             }
             const double xi = act ? s_x[is] : 0.0, yi = act ? s_y[is] : 0.0, zi = act ? s_z[is] : 0.0;
+            // Candidates are tested first; a lane queues the staged index of each
+            // one in range and, once some lane's queue is full, the warp evaluates
+            // the queued force terms, each lane in its own candidate order.  So
+            // the FP64 force arithmetic runs on (nearly) full warps, not once per
+            // candidate trip in which any lane has a pair in range.
+            int *myq = reinterpret_cast<int *>(smem + Ly.queue) + warp * 32 * kQueueDepth + lane;
+            int nq = 0;
+            auto drain = [&]() {
+                const int nmax = __reduce_max_sync(kFull, nq);
+                for (int i = 0; i < nmax; ++i)
+                    if (i < nq) {
+                        const int q = myq[32 * i];
+                        pair_f64<OBS>(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.ushift, a64);
+                    }
+                nq = 0;
+            };
+            auto offer = [&](bool valid, int q) {   // warp-wide: every lane calls it
+                if (valid && in_range_f64(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.rc2)) myq[32 * nq++] = q;
+                if (__any_sync(kFull, nq == kQueueDepth)) drain();
+            };
             for (int ox = -1; ox <= 1; ++ox)
                 for (int oy = -1; oy <= 1; ++oy)
                     for (int oz = -1; oz <= 1; ++oz) {
                         const int kn = ((hx + 1 + ox) * EY + (hy + 1 + oy)) * EZ + (hz + 1 + oz);
                         const int cs = s_start[kn], cn = s_cnt[kn];
                         if (kn == kh) {   // the home cell: every atom
-                            if (act)
-                                for (int t = g; t < cn; t += ns)
-                                    pair_f64<OBS>(xi, yi, zi, s_x[cs + t], s_y[cs + t], s_z[cs + t], B.rc2,
-                                                  B.ushift, a64);
+                            for (int b = 0; b < cn; b += ns) offer(act && b + g < cn, cs + b + g);
                             continue;
                         }
                         // the cell's atoms within the cutoff of the box, in order (at most
@@ -708,13 +738,13 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                             m += __popc(kept);
                         }
                         __syncwarp();
-                        if (act)
-                            for (int e = g; e < m; e += ns) {
-                                const int q = plist[e];
-                                pair_f64<OBS>(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.rc2, B.ushift, a64);
-                            }
-                        __syncwarp();
+                        for (int b = 0; b < m; b += ns) {
+                            const bool v = act && b + g < m;
+                            offer(v, v ? plist[b + g] : 0);
+                        }
+                        __syncwarp();   // the queue holds staged indices: plist may be rewritten
                     }
+            drain();
             // combine the ns partial sums of each home atom in split order
             double fx = a64.fx, fy = a64.fy, fz = a64.fz, uu = a64.u, ww = a64.w;
             if (ns > 1) {
