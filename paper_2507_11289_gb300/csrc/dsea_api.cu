@@ -345,8 +345,9 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     hb.w_is_sync = 1;
     hb.withhold_slice = -1;
     hb.wait_limit_ns = 5000000000LL;   // 5 s
-    // work-unit shape: requested, cached by the autotuner, or a default (mixed
-    // form: 2 x 4 home cells per warp; FP64 form: 4 x 4 cells per CTA)
+    // work-unit shape: requested, cached by the autotuner, or the default of
+    // 2 x 4 home cells (per warp in the mixed form, per CTA in the FP64 form,
+    // where it keeps two CTAs' staging in one SM's shared memory)
     int ty = p.tile_y, tz = p.tile_z;
     if (ty == 0 || tz == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -355,7 +356,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
             ty = it->second.first;
             tz = it->second.second;
         } else {
-            ty = ty ? ty : (p.precision == DSEA_MIXED ? 2 : 4);
+            ty = ty ? ty : 2;
             tz = tz ? tz : 4;
         }
     }

@@ -90,7 +90,7 @@ __device__ __forceinline__ float inv_of(int d)
 
 // Shared-memory carve-up of one FP64 unit.
 struct Layout {
-    size_t cnt, nst, start, gcell, atoms, id, slot, scr, queue, red, cellke, lam, ctr, total;
+    size_t cnt, nst, start, gcell, atoms, atomsf, id, slot, scr, queue, red, cellke, lam, band, ctr, total;
 };
 
 // Depth of the per-lane queue of in-range candidates in the FP64 pair loop.
@@ -106,6 +106,7 @@ __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
     L.gcell = o; o += sizeof(int) * staged_cells;
     o = align16(o);
     L.atoms = o; o += 3 * sizeof(double) * smem_atoms;   // x[], y[], z[]
+    L.atomsf = o; o += 3 * sizeof(float) * smem_atoms;   // FP32 copies relative to the unit's corner
     L.id = o;    o += sizeof(int) * smem_atoms;
     L.slot = o;  o += sizeof(int) * smem_atoms;
     o = align16(o);
@@ -114,6 +115,7 @@ __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
     L.red = o;   o += sizeof(double) * kWarps * 4;
     L.cellke = o; o += sizeof(double) * 2 * staged_cells;   // thermostat: (KE, N) per home cell
     L.lam = o;   o += 16;
+    L.band = o;  o += 16;                               // FP32 pre-test thresholds
     L.ctr = o;   o += 16;
     L.total = align16(o);
     return L;
@@ -491,11 +493,15 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
     double *s_red = reinterpret_cast<double *>(smem + Ly.red);
     double *s_cellke = reinterpret_cast<double *>(smem + Ly.cellke);
     double *s_lam = reinterpret_cast<double *>(smem + Ly.lam);
+    float *s_band = reinterpret_cast<float *>(smem + Ly.band);
     int *s_ctr = reinterpret_cast<int *>(smem + Ly.ctr);
     const bool thermo = INTEGRATE && B.T0 > 0.0;   // uniform across the CTA
     double *s_x = reinterpret_cast<double *>(smem + Ly.atoms);
     double *s_y = s_x + B.smem_atoms;
     double *s_z = s_y + B.smem_atoms;
+    float *s_xf = reinterpret_cast<float *>(smem + Ly.atomsf);
+    float *s_yf = s_xf + B.smem_atoms;
+    float *s_zf = s_yf + B.smem_atoms;
     int *s_id = reinterpret_cast<int *>(smem + Ly.id);
 
     // unit geometry
@@ -509,7 +515,15 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 inv_nz = inv_of(nz), inv_cps = inv_of(B.cps);
 
     // 1. counts of the staged cells
-    if (tid == 0) *s_ctr = 0;
+    if (tid == 0) {
+        *s_ctr = 0;
+        // the pair loop's FP32 pre-test: band, rc2 + band, rc2 - band (see there)
+        const double E = fmax((nx + 2) * B.lc[0], fmax((ny + 2) * B.lc[1], (nz + 2) * B.lc[2]));
+        const double band = 4.0 * (6.0 * sqrt(B.rc2) * E + 3.0 * B.rc2) * 0x1p-24;
+        s_band[0] = (float)band;
+        s_band[1] = (float)(B.rc2 + band);
+        s_band[2] = (float)(B.rc2 - band);
+    }
     for (int k = tid; k < n_staged; k += kThreads) {
         const int lx = qdiv(k, inv_eyez), rem = k - lx * EY * EZ, ly = qdiv(rem, inv_ez), lz = rem - ly * EZ;
         const int gx = wrap_index(x0 - 1 + lx, B.nc[0]);
@@ -557,6 +571,9 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
     // 3. stage atoms in each cell's canonical order: the stayers (front
     // slots) as they are, then the arrivals (back slots) ordered by atom id
     const long long S = B.n_slots;
+    // the unit's lower corner in the staged frame: FP32 copies relative to it
+    // serve the exact-by-construction cutoff pre-test of the pair loop
+    const double ref_x = (x0 - 1) * B.lc[0], ref_y = (y0 - 1) * B.lc[1], ref_z = (z0 - 1) * B.lc[2];
     for (int k = warp; k < n_staged; k += kWarps) {
         const int c = s_cnt[k];
         if (c == 0) continue;
@@ -572,9 +589,14 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         for (int a = lane; a < n_s; a += 32) {
             const long long slot = base + a;
             s_slot[st + a] = (int)slot;
-            s_x[st + a] = __ldcg(B.r[p] + slot) + shx;
-            s_y[st + a] = __ldcg(B.r[p] + S + slot) + shy;
-            s_z[st + a] = __ldcg(B.r[p] + 2 * S + slot) + shz;
+            const double x = __ldcg(B.r[p] + slot) + shx, y = __ldcg(B.r[p] + S + slot) + shy,
+                         z = __ldcg(B.r[p] + 2 * S + slot) + shz;
+            s_x[st + a] = x;
+            s_y[st + a] = y;
+            s_z[st + a] = z;
+            s_xf[st + a] = (float)(x - ref_x);
+            s_yf[st + a] = (float)(y - ref_y);
+            s_zf[st + a] = (float)(z - ref_z);
             s_id[st + a] = __ldcg(B.id[p] + slot);
         }
         if (n_a == 0) continue;
@@ -622,6 +644,9 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 s_x[dst] = xm[m];
                 s_y[dst] = ym[m];
                 s_z[dst] = zm[m];
+                s_xf[dst] = (float)(xm[m] - ref_x);
+                s_yf[dst] = (float)(ym[m] - ref_y);
+                s_zf[dst] = (float)(zm[m] - ref_z);
                 s_id[dst] = idm[m];
             }
         }
@@ -697,6 +722,13 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             // candidate trip in which any lane has a pair in range.
             int *myq = reinterpret_cast<int *>(smem + Ly.queue) + warp * 32 * kQueueDepth + lane;
             int nq = 0;
+            // FP32 pre-test.  The FP32 coordinates (|x| <= E, the unit's extent)
+            // carry an error of at most E 2^-24 each, so near the cutoff (|d| <= rc)
+            // the FP32 r2 differs from the FP64 one by less than
+            // (6 rc E + 3 rc^2) 2^-24; four times that is the band.  Outside
+            // (band, rc2 - band) and above rc2 + band the FP64 test would decide
+            // the same way; in between it decides.
+            const float xif = act ? s_xf[is] : 0.f, yif = act ? s_yf[is] : 0.f, zif = act ? s_zf[is] : 0.f;
             auto drain = [&]() {
                 const int nmax = __reduce_max_sync(kFull, nq);
                 for (int i = 0; i < nmax; ++i)
@@ -707,7 +739,15 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 nq = 0;
             };
             auto offer = [&](bool valid, int q) {   // warp-wide: every lane calls it
-                if (valid && in_range_f64(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.rc2)) myq[32 * nq++] = q;
+                if (valid) {
+                    const float dx = xif - s_xf[q], dy = yif - s_yf[q], dz = zif - s_zf[q];
+                    const float r2f = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    bool in;
+                    if (r2f > s_band[1]) in = false;
+                    else if (r2f < s_band[2] && r2f > s_band[0]) in = true;
+                    else in = in_range_f64(xi, yi, zi, s_x[q], s_y[q], s_z[q], B.rc2);
+                    if (in) myq[32 * nq++] = q;
+                }
                 if (__any_sync(kFull, nq == kQueueDepth)) drain();
             };
             for (int ox = -1; ox <= 1; ++ox)
