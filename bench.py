@@ -40,6 +40,7 @@ PAIRS_PER_ATOM = lambda rho: rho * 4.0 * math.pi / 3.0 * 2.5 ** 3   # directed p
 FLOPS_PER_PAIR = 27                # FP32 flops counted per directed in-cutoff pair
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (TFLOP/s); no measured FP64 peak exists
 PROFILE = os.path.join(ROOT, "profiles", "k_ring_mixed_1m.md")
 
 
@@ -474,8 +475,12 @@ def main():
                                   flush_buf, stream)
         sec64 = max_over_ranks(sec64, world)
         v64 = sum_over_ranks(spec.n_atoms * args.md_steps * args.fp64_steps, world) / sec64
+        ach64 = v64 * flops_per_atom_step / 1e12
         line["fp64"] = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
-                        "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64}
+                        "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64,
+                        "roofline": {"bound": "fp64", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                                     "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                                     "peak_note": "nominal GB300 FP64 rate (no measured FP64 peak)"}}
     if "walls" not in skip:
         sec_w, _, _, _ = time_box(dsea, torch, spec, dsea.MIXED, args.walls_steps, 3, args.md_steps,
                                   flush_buf, stream, walls=True)
