@@ -1148,33 +1148,39 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
     // rounding margin) of the box, which holds every home atom; a dropped
     // entry is out of range of all of them, so its pair terms would all have
     // been masked to zero.  Kept entries are compacted in order into the
-    // pair layout, in place: an entry never moves up, and each 32-entry
-    // sweep writes below the entries the next sweep reads.
+    // pair layout, in place: an entry never moves up, and each 64-entry
+    // sweep (two entries per lane, which overlaps their loads and tests) writes
+    // below the entries the next sweep reads.
     const float reach2 = B.rc2f + kReachMargin;
     const unsigned below = (1u << lane) - 1u;
     int m = k0;
-    for (int e0 = k0; e0 < n_raw; e0 += 32) {
-        const int e = e0 + lane;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool keep = false;
-        if (e < n_raw) {
-            a = raw[e];
-            // into the home cell's frame: the same FP32 sum as shifting by ox lc
-            // (ox lc is exact); a padding entry (tag 0) stays far away
-            const float4 o = g_offsets[__float_as_int(a.w) & 31];
-            const volatile float *lc = B.lcf;
-            a.x = fmaf(o.x, lc[0], a.x);
-            a.y = fmaf(o.y, lc[1], a.y);
-            a.z = fmaf(o.z, lc[2], a.z);
-            keep = box_dist2(a.x, a.y, a.z, lo, hi) <= reach2;
-        }
-        const unsigned kept = __ballot_sync(kFull, keep);
+    auto load_test = [&](int e, float4 &a) -> bool {
+        if (e >= n_raw) return false;
+        a = raw[e];
+        // into the home cell's frame: the same FP32 sum as shifting by ox lc
+        // (ox lc is exact); a padding entry (tag 0) stays far away
+        const float4 o = g_offsets[__float_as_int(a.w) & 31];
+        const volatile float *lc = B.lcf;
+        a.x = fmaf(o.x, lc[0], a.x);
+        a.y = fmaf(o.y, lc[1], a.y);
+        a.z = fmaf(o.z, lc[2], a.z);
+        return box_dist2(a.x, a.y, a.z, lo, hi) <= reach2;
+    };
+    for (int e0 = k0; e0 < n_raw; e0 += 64) {   // two entries per lane per sweep
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        const bool ka = load_test(e0 + lane, a), kb = load_test(e0 + 32 + lane, b);
+        const unsigned kA = __ballot_sync(kFull, ka), kB = __ballot_sync(kFull, kb);
         __syncwarp();
-        if (keep) {
-            float *d = list_entry(wa, m + __popc(kept & below));
+        if (ka) {
+            float *d = list_entry(wa, m + __popc(kA & below));
             d[0] = a.x; d[2] = a.y; d[4] = a.z; d[6] = a.w;
         }
-        m += __popc(kept);
+        m += __popc(kA);
+        if (kb) {
+            float *d = list_entry(wa, m + __popc(kB & below));
+            d[0] = b.x; d[2] = b.y; d[4] = b.z; d[6] = b.w;
+        }
+        m += __popc(kB);
     }
     if (m & 1) {   // pad the window to whole pairs
         if (lane == 0) {
