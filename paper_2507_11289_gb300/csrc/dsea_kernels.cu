@@ -94,7 +94,7 @@ struct Layout {
 };
 
 // Depth of the per-lane queue of in-range candidates in the FP64 pair loop.
-constexpr int kQueueDepth = 16;
+constexpr int kQueueDepth = 32;
 
 __host__ __device__ inline Layout make_layout(int staged_cells, int smem_atoms)
 {
