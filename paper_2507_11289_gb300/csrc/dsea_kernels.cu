@@ -470,8 +470,12 @@ __device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, do
 //   2. stages the atoms of those cells into shared memory in each cell's
 //      canonical order (stayers in slot order, then arrivals by atom id), as
 //      absolute positions shifted to the periodic image next to the unit,
+//      with FP32 copies relative to the unit's corner,
 //   3. computes, warp per home cell, the force on each home atom from the 27
-//      neighbour cells (Algorithm 1's first loop, Sec. 4.1 "md_v3a"),
+//      neighbour cells (Algorithm 1's first loop, Sec. 4.1 "md_v3a"): per
+//      neighbour cell the candidates near the home atoms' bounding box, their
+//      cutoff tests settled in FP32 where provably exact, the force terms of
+//      the pairs in range queued per lane and evaluated on full warps,
 //   4. (INTEGRATE) kicks and drifts each home atom (Algorithm 1's second and
 //      third loops) and writes it to the cell it moved to in the next-step
 //      buffer, which may belong to slice j-1, j or j+1 (O_out = 1, Sec. 4),
