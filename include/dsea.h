@@ -264,14 +264,15 @@ int dsea_server_destroy(dsea_server *srv);
  *   precision DSEA_FP64 or DSEA_MIXED;
  *   forces_dev device, 3 n_atoms FP64 output (atom-ID order);
  *   obs3_dev  device, 3 FP64 outputs (U, W, KE), or NULL;
- *   cuda_stream work is queued there; the call returns when it has finished.
+ *   cuda_stream work is queued there; before returning, the call waits for
+ *             that stream (and only that stream) to finish, because it reads
+ *             a status word back to the host.
  * Returns DSEA_ERR_SCRATCH_LIMIT, before touching the GPU, when the box needs
  * more than the 64 MiB (at density 0.8: about 290,000 atoms in FP64, 240,000
- * in the mixed form).  The
- * first call on a device looks up the array's device address (make it before
- * any stream capture).  Every call shares the array: calls that overlap on the
- * GPU, from other streams or host threads, race and must be serialised by
- * the caller. */
+ * in the mixed form).  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture.  Every call shares
+ * the array: calls that overlap on the GPU, from other streams or host
+ * threads, race and must be serialised by the caller. */
 #define DSEA_ERR_SCRATCH_LIMIT -11 /* problem larger than the fixed scratch */
 int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev, int64_t n_atoms,
                         const double *box, double rc, int precision, double *forces_dev,

@@ -1422,6 +1422,12 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, O
         const int hx = v.hx, hy = v.hy, hz = v.hz;
         int total = 0;
         const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), hx, hy, hz, lane, total);
+        if (__shfl_sync(kFull, c.n_s + c.n_a, 0) == 0) {   // an empty home cell only publishes its count
+            if (INTEGRATE && lane == 0)
+                B.cnt[(int)(s_abs & 1) ^ 1][c.gc] = (unsigned long long)(unsigned)(s_abs + 2) << 32;
+            __syncwarp();
+            return;
+        }
         build_window(B, (int)(s_abs & 1), c, total, 0, lane, wa);
         if (lane == 0) {
             wa.n_home = c.n_s + c.n_a;

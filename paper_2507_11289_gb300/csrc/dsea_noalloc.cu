@@ -120,9 +120,12 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     if (e == cudaSuccess) e = dsea::launch_bin(hb, db, pos_dev, vel_dev, st);
     if (e == cudaSuccess) e = dsea::launch_force_pass(hb, db, st);
     if (e == cudaSuccess && obs3_dev) e = dsea::launch_obs_reduce(hb.unit_obs, units, obs3_dev, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // the status word comes back on the caller's stream, and only that stream
+    // is waited for (a plain cudaMemcpy would also wait for every blocking
+    // stream of the device)
     int code = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&code, hb.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&code, hb.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return DSEA_ERR_CUDA;

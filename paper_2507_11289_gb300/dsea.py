@@ -452,6 +452,9 @@ class Box:
     def info(self):
         return box_get_info(self.h)
 
+    def debug_set(self, key, value):
+        debug_set(self.h, key, value)
+
     def autotune(self, trial_steps=5):
         return autotune(self.h, trial_steps)
 

@@ -141,6 +141,8 @@ def test_mixed_energy_drift_1000_steps(melted_4k):
             b.advance(10)
         o = b.observables()
         e_gpu.append((o["U"] + o["KE"]) / n)
+        r_end = b.positions()
+        F_end = b.forces()
     _, _, _, obs = oracle.run(pos, vel, box, steps=1000)
     e_ora = (obs[::10, 0] + obs[::10, 2]) / n
     e_gpu = np.array(e_gpu)
@@ -148,7 +150,14 @@ def test_mixed_energy_drift_1000_steps(melted_4k):
     drift_ora = abs(e_ora[-10:].mean() - e_ora[:10].mean())
     print(f"drift per atom over 1000 steps: mixed {drift_gpu:.3e}, oracle FP64 {drift_ora:.3e}; "
           f"max |E-E0| mixed {np.abs(e_gpu - e_gpu[0]).max():.3e}")
-    assert drift_gpu <= max(1e-4, 2.0 * drift_ora)
+    # the stated bar, flat: the periodic box's FP64 drift is far below it
+    assert drift_gpu <= 1e-4
+    # the per-step force gate at the end of the run, where the configuration
+    # is furthest from the lattice: the oracle's forces at the GPU's positions
+    Fo_end, _, _ = oracle.forces(r_end, box, RC, "cells")
+    e_rms, e_max = force_err(F_end, Fo_end)
+    print(f"mixed force error after 1000 steps: rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= 2e-6
 
 
 def test_smallest_box_and_ragged_units():
@@ -214,8 +223,29 @@ def test_full_1m_box_sampled_atoms(precision):
         assert info["n_slices"] == 43 and info["cells"] == [43, 43, 43]
         Fg = b.forces()
     tol = 1e-12 if precision == dsea.FP64 else 2e-6
-    assert rms(Fg[idx] - Fo) <= tol * rms(Fo)
+    e_rms, e_max = force_err(Fg[idx], Fo)
+    print(f"1M box, precision {precision}: force error rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= tol
     assert np.abs(Fg.sum(0)).max() <= (1e-9 if precision == dsea.FP64 else 1e-3) * rms(Fg) * np.sqrt(len(pos))
+
+
+def test_1m_box_after_20_mixed_steps():
+    """The 1M box after 20 mixed ring steps from the jittered lattice (a
+    disordered state): forces at 256 sampled atoms against the oracle at the
+    GPU's positions."""
+    spec = inputs.FLUID_1M
+    pos, vel, box = spec.state()
+    pos = inputs.jitter(pos, box, 0.1, 19)
+    rng = np.random.Generator(np.random.PCG64(9))
+    idx = np.sort(rng.choice(len(pos), 256, replace=False))
+    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+        b.advance(20)
+        r = b.positions()
+        F = b.forces()
+    Fo, _, _ = oracle.forces_subset(r, box, idx, RC)
+    e_rms, e_max = force_err(F[idx], Fo)
+    print(f"1M box after 20 steps: force error rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= 2e-6
 
 
 def test_full_67m_box_sampled_atoms():
@@ -235,12 +265,16 @@ def test_full_67m_box_sampled_atoms():
         r1 = b.positions()
         F1 = b.forces()
     Fo, _, _ = oracle.forces_subset(pos, box, idx, RC)
-    assert rms(Fg[idx] - Fo) <= 2e-6 * rms(Fo)
+    e_rms, e_max = force_err(Fg[idx], Fo)
+    print(f"67M box: force error rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= 2e-6
     assert np.abs(Fg.sum(0)).max() <= 1e-3 * rms(Fg) * np.sqrt(len(pos))
     del Fg
     # one step later: the sampled atoms' forces at the GPU's new positions
     F1o, _, _ = oracle.forces_subset(r1, box, idx, RC)
-    assert rms(F1[idx] - F1o) <= 2e-6 * rms(F1o)
+    e_rms, e_max = force_err(F1[idx], F1o)
+    print(f"67M box after one step: force error rms {e_rms:.3e}  max {e_max:.3e} (of rms force)")
+    assert e_rms <= 2e-6
 
 
 @pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
