@@ -38,9 +38,7 @@ UNIT = "atom-steps/s"
 MD_STEPS = 100                     # MD steps per bench step
 PAIRS_PER_ATOM = lambda rho: rho * 4.0 * math.pi / 3.0 * 2.5 ** 3   # directed pairs within rc
 FLOPS_PER_PAIR = 27                # FP32 flops counted per directed in-cutoff pair
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (TFLOP/s); no measured FP64 peak exists
+FP32_LANES = 128                   # FP32 FMA lanes per SM
 PROFILE = os.path.join(ROOT, "profiles", "k_ring_mixed_1m.md")
 
 
@@ -304,40 +302,108 @@ def batch_run(dsea, torch, n_boxes, md_steps, stream):
             b.close()
 
 
-def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100):
+def _union_length(intervals):
+    """Total length of the union of [a, b) intervals (time with a job in the system)."""
+    total, end = 0.0, -math.inf
+    for a, b in sorted(intervals):
+        if b <= end:
+            continue
+        total += b - max(a, end)
+        end = b
+    return total
+
+
+def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100, why_window=None):
     """Poisson job stream into the continuous-batching server; latency from
-    arrival (submit) to completion on the server clock."""
+    arrival (submit) to completion on the server clock.  Every job's state is
+    generated before the arrival window opens, so submissions keep to the
+    Poisson arrival times (host memory: the window's jobs, a few GB)."""
     from paper_2507_11289_gb300 import inputs
     jobs = inputs.served_stream(rate_per_s=rate, duration_s=duration, seed=seed)
+    states = [job.spec.state() for job in jobs]
     srv = dsea.server_create(int(budget_gb * 2 ** 30),
                              dsea.make_params(precision=dsea.MIXED), segment, 0)
     ids = []
+    late = []
     try:
         t0 = time.perf_counter()
         offered = 0.0
-        for job in jobs:
-            pos, vel, box = job.spec.state()
+        for job, (pos, vel, box) in zip(jobs, states):
             while time.perf_counter() - t0 < job.arrival_s:
-                time.sleep(0.0005)
+                time.sleep(0.0002)
+            late.append(time.perf_counter() - t0 - job.arrival_s)
             ids.append((dsea.server_submit(srv, pos, vel, box, job.spec.steps), job.spec.n_atoms))
             offered += job.spec.n_atoms * job.spec.steps
+        submit_s = time.perf_counter() - t0
         dsea.server_drain(srv)
         wall = time.perf_counter() - t0
-        lat = []
+        lat, spans = [], []
         for jid, n in ids:
             _, _, _, ta, td = dsea.server_result(srv, jid, n)
             lat.append(td - ta)
+            spans.append((ta, td))
         st = dsea.server_stats(srv)
     finally:
         dsea.server_destroy(srv)
     lat = np.array(lat)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "jobs": len(ids), "rate_per_s": rate, "arrival_window_s": duration,
-            "atom_steps_per_s": st["atom_steps"] / wall, "busy_atom_steps_per_s":
-            st["atom_steps"] / max(st["busy_seconds"], 1e-9), "offered_atom_steps_per_s":
-            offered / duration, "launches": st["launches"], "budget_gb": budget_gb,
-            "workload": "Poisson arrivals; fcc LJ boxes N log-uniform 1e3-2e6, rho U(0.3,0.9), "
-                        "T U(0.8,2.5), steps log-uniform 100-10,000; mixed"}
+    occupied = _union_length(spans)
+    out = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "jobs": len(ids), "rate_per_s": rate, "arrival_window_s": duration,
+           "achieved_arrival_rate_per_s": len(ids) / max(submit_s, 1e-9),
+           "max_submit_lateness_s": float(max(late)) if late else 0.0,
+           "atom_steps_per_s": st["atom_steps"] / wall,
+           "occupied_atom_steps_per_s": st["atom_steps"] / max(occupied, 1e-9),
+           "busy_atom_steps_per_s": st["atom_steps"] / max(st["busy_seconds"], 1e-9),
+           "offered_atom_steps_per_s": offered / duration, "drain_s": wall - submit_s,
+           "launches": st["launches"], "budget_gb": budget_gb,
+           "workload": "Poisson arrivals; fcc LJ boxes N log-uniform 1e3-2e6, rho U(0.3,0.9), "
+                       "T U(0.8,2.5), steps log-uniform 100-10,000; mixed"}
+    if why_window:
+        out["window_note"] = why_window
+    return out
+
+
+def device_peaks(dsea, torch, stream):
+    """The roofline denominators: the FP32 and FP64 FMA rates measured by the
+    library's probe on this GPU, beside the FP32 rate derived from the
+    device's SM count and maximum SM clock (both queried, not assumed)."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    max_mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()),
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        max_mhz = float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    derived = sms * FP32_LANES * 2 * max_mhz * 1e6 / 1e12 if max_mhz else None
+    return {"fp32_measured": dsea.probe_peak(dsea.PROBE_FP32, stream),
+            "fp32x2_measured": dsea.probe_peak(dsea.PROBE_FP32X2, stream),
+            "fp64_measured": dsea.probe_peak(dsea.PROBE_FP64, stream),
+            "fp32_derived": derived, "sms": sms, "sm_max_mhz": max_mhz}
+
+
+def cpu_model():
+    """The host CPU's model name and logical core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    if not name:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return name or "unknown", os.cpu_count()
 
 
 def profile_traffic_per_atom_step():
@@ -352,19 +418,27 @@ def profile_traffic_per_atom_step():
     return None
 
 
-def cpu_baseline(spec, sample_steps):
-    """The CPU oracle as it stands (plain C, one thread) on a bounded sample:
+def cpu_baseline(spec, sample_steps, threads=0):
+    """The CPU oracle as it stands (plain C, its force loop shared among
+    `threads` OpenMP threads, 0 = all cores) on a bounded sample:
     `sample_steps` velocity-Verlet steps of the same box."""
     import oracle
     pos, vel, box = spec.state()
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.run(pos, vel, box, steps=sample_steps)
-    dt = time.perf_counter() - t0
+    n_all = oracle.set_threads(0)
+    used = oracle.set_threads(threads if threads > 0 else n_all)
+    try:
+        t0 = time.perf_counter()
+        oracle.run(pos, vel, box, steps=sample_steps)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(n_all)
+    model, logical = cpu_model()
     # the oracle run does sample_steps + 1 force evaluations (closing pass included)
-    return {"value": len(pos) * sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": len(pos) * sample_steps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "cpu": model, "host_logical_cores": logical,
             "sample": f"{sample_steps} velocity-Verlet steps of the {len(pos):,}-atom box "
-                      f"({dt:.1f} s, single thread, cell-list oracle)"}
+                      f"({dt:.1f} s, {used} thread{'s' if used != 1 else ''}, cell-list oracle)"}
 
 
 def reference_arm(args, rank, world):
@@ -376,6 +450,8 @@ def reference_arm(args, rank, world):
     n = spec.n_atoms
     import oracle
     oracle.build()
+    cores = oracle.set_threads(0)
+    model, _ = cpu_model()
     pos, vel, box = spec.state()
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -391,9 +467,9 @@ def reference_arm(args, rank, world):
             "config": {"workload": f"LJ fluid {n:,} atoms (64^3 fcc), rho 0.8, T 1.5, rc 2.5, "
                                    f"dt 0.005; each step = {args.ref_md_steps} velocity-Verlet "
                                    f"steps of the CPU FP64 oracle (bounded sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
                              "sample": f"{args.ref_md_steps} oracle steps per bench step, "
-                                       f"{len(per)} timed steps, single thread"},
+                                       f"{len(per)} timed steps, {cores} OpenMP threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -406,12 +482,17 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--md-steps", type=int, default=MD_STEPS)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--ref-md-steps", type=int, default=2)
+    ap.add_argument("--ref-md-steps", type=int, default=10)
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--cpu-sample-steps-all", type=int, default=40,
+                    help="oracle steps of the all-cores CPU baseline")
     ap.add_argument("--batch-boxes", type=int, default=512)
     ap.add_argument("--batch-md-steps", type=int, default=2000)
-    ap.add_argument("--serve-rate", type=float, default=8.0)
-    ap.add_argument("--serve-window", type=float, default=8.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-window", type=float, default=1.0,
+                    help="arrival window of the configured stream (s); 60 s would take about half an "
+                         "hour to drain on one GPU")
+    ap.add_argument("--serve-window-sustainable", type=float, default=8.0)
     ap.add_argument("--serve-rate-sustainable", type=float, default=2.5,
                     help="arrival rate of the second served run (about 0.7 utilisation)")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
@@ -452,13 +533,22 @@ def main():
     flops_per_atom_step = PAIRS_PER_ATOM(spec.rho) * FLOPS_PER_PAIR
     achieved = spec.n_atoms * args.md_steps * flops_per_atom_step / launch_s / 1e12
     tpa = profile_traffic_per_atom_step()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
+    peaks = device_peaks(dsea, torch, stream)
+    fp32_peak = peaks["fp32_measured"]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
                 "traffic": None if tpa is None else tpa * spec.n_atoms * args.md_steps,
                 "kernel": "k_ring_mixed (warp-level ring, mixed form)",
                 "counted": f"{FLOPS_PER_PAIR} flops x {PAIRS_PER_ATOM(spec.rho):.2f} directed "
                            f"in-cutoff pairs per atom-step",
-                "peak_note": "FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+                "peak_note": (f"FP32 peak measured on this GPU by dsea_probe_peak (scalar FMA chains on all "
+                              f"{peaks['sms']} SMs): {fp32_peak:.1f} TFLOP/s; derived from the queried SM "
+                              f"count and maximum SM clock ({peaks['sms']} x 128 lanes x 2 x "
+                              f"{peaks['sm_max_mhz']} MHz): "
+                              + (f"{peaks['fp32_derived']:.1f}" if peaks["fp32_derived"] else "n/a")
+                              + f" TFLOP/s; packed FP32x2 FMAs measured at {peaks['fp32x2_measured']:.1f}"),
+                "frac_of_derived": achieved / peaks["fp32_derived"] if peaks["fp32_derived"] else None,
+                "peaks": peaks}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sec_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
@@ -476,11 +566,12 @@ def main():
         sec64 = max_over_ranks(sec64, world)
         v64 = sum_over_ranks(spec.n_atoms * args.md_steps * args.fp64_steps, world) / sec64
         ach64 = v64 * flops_per_atom_step / 1e12
+        fp64_peak = peaks["fp64_measured"]
         line["fp64"] = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
                         "ms_per_step": 1e3 * sec64 / args.fp64_steps, "mixed_over_fp64": value / v64,
-                        "roofline": {"bound": "fp64", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
-                                     "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
-                                     "peak_note": "nominal GB300 FP64 rate (no measured FP64 peak)"}}
+                        "roofline": {"bound": "fp64", "achieved": ach64, "peak": fp64_peak,
+                                     "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+                                     "peak_note": "FP64 FMA rate measured on this GPU by dsea_probe_peak"}}
     if "walls" not in skip:
         sec_w, _, _, _ = time_box(dsea, torch, spec, dsea.MIXED, args.walls_steps, 3, args.md_steps,
                                   flush_buf, stream, walls=True)
@@ -512,7 +603,7 @@ def main():
         v_b = sum_over_ranks(big.n_atoms * big.steps, world) / sec_b
         ach_b = big.n_atoms * big.steps * PAIRS_PER_ATOM(big.rho) * FLOPS_PER_PAIR / sec_b / 1e12
         line["box_67m"] = {"value": v_b, "unit": UNIT, "md_steps": big.steps, "seconds": sec_b,
-                           "roofline_frac": ach_b / FP32_PEAK_TFLOPS, "achieved_tflops": ach_b,
+                           "roofline_frac": ach_b / fp32_peak, "achieved_tflops": ach_b,
                            "workload": "LJ fluid 67,108,864 atoms (256^3 fcc), rho 0.8, T 1.5, 175 "
                                        "x-slices, mixed, ring schedule, one 200-step advance",
                            "unit_shape": [info_b["tile_y"], info_b["tile_z"]],
@@ -520,15 +611,23 @@ def main():
     if "batch" not in skip:
         line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream)
     if "serve" not in skip:
-        line["served"] = serve_run(dsea, torch, args.serve_rate, args.serve_window, args.serve_budget_gb)
-        line["served_sustainable"] = serve_run(dsea, torch, args.serve_rate_sustainable, args.serve_window,
-                                               args.serve_budget_gb)
+        why = None
+        if args.serve_window < 60.0:
+            why = (f"arrival window {args.serve_window:g} s instead of 60 s: the stream offers about "
+                   f"1.1e11 atom-steps/s (200 jobs/s x E[N steps] 5.6e8), some 30 times what one GPU "
+                   f"advances, so the 60 s stream would take about half an hour to drain; the shorter "
+                   f"window keeps the arrival process (rate, size and step draws) and the queueing it causes")
+        line["served"] = serve_run(dsea, torch, args.serve_rate, args.serve_window, args.serve_budget_gb,
+                                   why_window=why)
+        line["served_sustainable"] = serve_run(dsea, torch, args.serve_rate_sustainable,
+                                               args.serve_window_sustainable, args.serve_budget_gb)
     if "dataset" not in skip:
         line["dataset_heat1d"] = dataset_run(dsea, torch, stream)
     if "e2e" not in skip:
         line["e2e"] = e2e_run(dsea, torch, spec, dsea.MIXED, 3, args.md_steps, stream)
     if rank == 0 and world == 1 and "cpu" not in skip:
-        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample_steps)
+        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample_steps_all, threads=0)
+        line["cpu_baseline_1core"] = cpu_baseline(spec, args.cpu_sample_steps, threads=1)
     line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)

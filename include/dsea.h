@@ -139,7 +139,10 @@ typedef struct {
  * provides slices of the dataset"; Sec. 4 geometry).  The box is cut into
  * n_slices slices along x of width Lx / n_slices >= rc and into cells of edge
  * >= rc; needs >= 3 slices and >= 3 cells per axis (checked by
- * dsea_register_kernel, which knows rc).  The positions and velocities are
+ * dsea_register_kernel, which knows rc).  The cell count per axis is the
+ * paper's floor(L / rc) at liquid density; below rho = 8 / rc^3 the cells
+ * grow (edge (8 / rho)^(1/3), at most 1.5 rc, still at least 3 per axis) so
+ * that each holds about eight atoms.  The positions and velocities are
  * copied to device buffers owned by the box (through `allocator`) and the
  * positions checked there; the call returns once the copies are complete, so
  * the caller may reuse its arrays at once (pinned host memory makes the
@@ -277,6 +280,22 @@ int dsea_server_destroy(dsea_server *srv);
 int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev, int64_t n_atoms,
                         const double *box, double rc, int precision, double *forces_dev,
                         double *obs3_dev, void *cuda_stream);
+
+/* ---- arithmetic peak probes ---------------------------------------------- */
+
+/* The paper has no counterpart to this call: it measures the denominators of
+ * the roofline the benchmark reports.  kind DSEA_PROBE_FP32: scalar FP32
+ * fused multiply-adds (2 flops each); DSEA_PROBE_FP32X2: packed two-lane FP32
+ * FMAs (fma.rn.f32x2, 4 flops each); DSEA_PROBE_FP64: FP64 FMAs.  8 CTAs of
+ * 256 threads per SM, 8 independent chains per thread; *tflops receives the
+ * counted flops over the CUDA-event time of one launch on `cuda_stream`
+ * (after an untimed warm-up launch).  The call allocates a small device
+ * buffer, waits for the stream and returns DSEA_OK, DSEA_ERR_INVALID_ARG,
+ * DSEA_ERR_NO_DEVICE or DSEA_ERR_CUDA. */
+#define DSEA_PROBE_FP32 0
+#define DSEA_PROBE_FP32X2 1
+#define DSEA_PROBE_FP64 2
+int dsea_probe_peak(int kind, void *cuda_stream, double *tflops);
 
 /* ---- failure-detection testing hooks -------------------------------------- */
 

@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-             "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+             "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -51,7 +51,8 @@ def build_variant(out_path: str, defines=()) -> str:
     """Compile lj_oracle.c with extra -D defines into out_path (the mutation
     tests plant deliberate mistakes this way; the oracle itself never does)."""
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", *[f"-D{d}" for d in defines], "-o", out_path, _SRC, "-lm"])
+                           "-fno-fast-math", "-fopenmp", *[f"-D{d}" for d in defines], "-o", out_path, _SRC,
+                           "-lm"])
     return out_path
 
 
@@ -85,6 +86,7 @@ def _configure(lib):
     lib.oracle_run_w.argtypes = [i64, p, p, p, d, d, i64, c, c, p, p]
     lib.oracle_run_ex.argtypes = [i64, p, p, p, d, d, i64, c, c, c, c, d, p, p, p]
     lib.oracle_profiles.argtypes = [i64, p, p, p, d, c, c, c, p]
+    lib.oracle_set_threads.argtypes = [c]
     for f in (lib.oracle_pair, lib.oracle_forces_brute, lib.oracle_forces_cells,
               lib.oracle_forces_subset, lib.oracle_run, lib.oracle_forces_brute_w,
               lib.oracle_forces_cells_w, lib.oracle_forces_subset_w, lib.oracle_run_w,
@@ -189,3 +191,9 @@ def profiles(pos, vel, box, n_cells_x: int, cells_per_slice: int, rc: float = 2.
     _check(_load().oracle_profiles(len(p), _ptr(p), None if v is None else _ptr(v), _ptr(b), rc,
                                    1 if walls else 0, n_cells_x, cells_per_slice, _ptr(out)))
     return out
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the OpenMP force loop (0: all cores, the default).  Results
+    do not depend on it.  Returns the count now in effect."""
+    return int(_load().oracle_set_threads(int(n)))

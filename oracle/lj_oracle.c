@@ -36,6 +36,9 @@
  *     the closing half kick, so the returned state is synchronised
  *     (r_n, v_n, F_n).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -241,7 +244,10 @@ static void atom_from_cells(int64_t i, const double *pos, const double *box, dou
     *w_half = ww;
 }
 
-/* Cell-list force on every atom (27-cell stencil, directed pairs). */
+/* Cell-list force on every atom (27-cell stencil, directed pairs).  The atoms
+ * are independent, so with OpenMP they are shared among threads; each atom's
+ * sum, and the U and W sums over atoms (taken afterwards in atom order), are
+ * the same with any thread count. */
 int oracle_forces_cells_w(int64_t n, const double *pos, const double *box, double rc, int walls_x,
                           double *F, double *U, double *W)
 {
@@ -249,17 +255,37 @@ int oracle_forces_cells_w(int64_t n, const double *pos, const double *box, doubl
     cell_list cl;
     int rcode = build_cells(n, pos, box, rc, &cl);
     if (rcode) return rcode;
-    double rc2 = rc * rc, ushift = lj_shift(rc), u_sum = 0.0, w_sum = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        double uh, wh;
-        atom_from_cells(i, pos, box, rc2, ushift, walls_x, &cl, &F[3 * i], &uh, &wh);
-        u_sum += uh;
-        w_sum += wh;
+    double *half = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+    if (!half) {
+        free_cells(&cl);
+        return ORACLE_ERR_OOM;
     }
+    double rc2 = rc * rc, ushift = lj_shift(rc), u_sum = 0.0, w_sum = 0.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        atom_from_cells(i, pos, box, rc2, ushift, walls_x, &cl, &F[3 * i], &half[2 * i], &half[2 * i + 1]);
+    for (int64_t i = 0; i < n; ++i) {
+        u_sum += half[2 * i];
+        w_sum += half[2 * i + 1];
+    }
+    free(half);
     free_cells(&cl);
     *U = u_sum;
     *W = w_sum;
     return ORACLE_OK;
+}
+
+/* Threads of the OpenMP force loop (n <= 0: the runtime's default, all
+ * cores); returns the count now in effect (1 without OpenMP). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int oracle_forces_cells(int64_t n, const double *pos, const double *box, double rc, double *F, double *U,

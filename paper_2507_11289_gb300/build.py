@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdsea.so")
-SOURCES = ["dsea_kernels.cu", "dsea_api.cu", "dsea_server.cu", "dsea_noalloc.cu", "dsea_dataset.cu"]
+SOURCES = ["dsea_kernels.cu", "dsea_api.cu", "dsea_server.cu", "dsea_noalloc.cu", "dsea_dataset.cu",
+           "dsea_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -295,16 +295,33 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     if (p.precision != DSEA_FP64 && p.precision != DSEA_MIXED) return DSEA_ERR_INVALID_ARG;
     if (p.schedule != DSEA_SCHED_RING && p.schedule != DSEA_SCHED_STEPWISE) return DSEA_ERR_INVALID_ARG;
     if (p.tile_y < 0 || p.tile_z < 0 || p.cell_capacity < 0 || p.ctas < 0) return DSEA_ERR_INVALID_ARG;
-    // geometry (Sec. 4): slices along x of width >= rc, cubic-ish cells >= rc
+    // geometry (Sec. 4): slices along x of width >= rc, cubic-ish cells >= rc.
+    // The paper's count floor(b / rc) per axis holds at liquid density; in a
+    // dilute box (below rho = 8 / rc^3, 0.51 at rc = 2.5) a cell of edge rc
+    // holds one or two atoms, and every home cell pays for gathering its
+    // 27-cell neighbourhood for them.  There the target edge grows to
+    // (8 / rho)^(1/3), at most 1.5 rc, so that a cell holds about eight atoms
+    // (more at the 1.5 rc limit's densities); the stencil stays 27 cells of
+    // edge >= rc, so every pair within rc is still met exactly once per atom.
+    const double vol_box = L[0] * L[1] * L[2];
+    const double rho = vol_box > 0.0 ? (double)n_atoms / vol_box : 0.0;
+    const double edge = rho > 0.0 ? std::min(1.5 * p.rc, std::max(p.rc, std::cbrt(8.0 / rho))) : 1.5 * p.rc;
+    auto cells_along = [&](double len) {   // edge near `edge`, within [rc, 1.5 rc]; at least 3 cells
+        const int n_max = (int)std::floor(len / p.rc);
+        int n = std::max((int)std::floor(len / edge), (int)std::ceil(len / (1.5 * p.rc)));
+        n = std::min(n, n_max);
+        return std::max(n, std::min(3, n_max));
+    };
     int n_s = n_slices_req, cps = 1;
     if (n_s == 0) {
-        n_s = (int)std::floor(L[0] / p.rc);
+        n_s = cells_along(L[0]);
     } else {
         const double w = L[0] / n_s;
         if (w < p.rc) return DSEA_ERR_INVALID_ARG;
-        cps = (int)std::floor(w / p.rc);
+        cps = (int)std::floor(w / edge);
+        if (cps < 1 || w / cps > 1.5 * p.rc) cps = (int)std::floor(w / p.rc);   // layers no wider than 1.5 rc
     }
-    const int ncy = (int)std::floor(L[1] / p.rc), ncz = (int)std::floor(L[2] / p.rc);
+    const int ncy = cells_along(L[1]), ncz = cells_along(L[2]);
     if (n_s < 3 || cps < 1 || (int64_t)n_s * cps < 3 || ncy < 3 || ncz < 3) return DSEA_ERR_INVALID_ARG;
     hb.n_slices = n_s;
     hb.cps = cps;

@@ -4,12 +4,20 @@
 // thread admits them while their estimated device footprint fits the memory
 // budget, creates and bins their boxes (state stays resident on the device),
 // and advances every resident box together in one persistent ring launch of
-// at most `segment_steps` steps per box.  Between launches, finished jobs are
-// read back and released and newly arrived jobs join, so jobs that arrive
-// while others run overlap with them on the device.  Each box is advanced by
-// exactly the arithmetic it would see alone: the kernels sum every force in
-// an order fixed by the box's own state, so a job's result does not depend on
-// which other jobs shared its launches.
+// at most `segment_steps` steps per box.  Jobs that arrive while others run
+// join between launches, so their work overlaps on the device.  Each box is
+// advanced by exactly the arithmetic it would see alone: the kernels sum every
+// force in an order fixed by the box's own state, so a job's result does not
+// depend on which other jobs shared its launches.
+//
+// The device never waits for the host's admission work: the ring segments
+// run on the compute stream while the host creates, uploads and bins newly
+// admitted boxes on a second (admission) stream and reads back the jobs that
+// finished in the previous segment there; an event orders each new box's
+// binning before the first segment that includes it.  Box memory comes from a
+// stream-ordered pool on the admission stream (cudaMallocFromPoolAsync /
+// cudaFreeAsync, kept by the pool between jobs), so admitting or releasing a
+// job never calls cudaMalloc or cudaFree, which would synchronise the device.
 #include "dsea_host.h"
 
 #include <algorithm>
@@ -43,7 +51,12 @@ struct dsea_server {
     size_t budget = 0;
     dsea_params params{};
     int segment = 100;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;    // compute stream: the ring segments
+    bool own_stream = false;
+    cudaStream_t astream = nullptr;   // admission stream: box creation, binning, read-back
+    cudaMemPool_t pool = nullptr;     // device memory of the boxes, on the admission stream
+    dsea_allocator alloc{};
+    cudaEvent_t ev_ready = nullptr;   // admission work done (new boxes binned)
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -82,12 +95,29 @@ void finish(dsea_server *s, Job *j, int state)
     s->cv_done.notify_all();
 }
 
+void *pool_alloc(size_t bytes, void *ctx)
+{
+    dsea_server *s = static_cast<dsea_server *>(ctx);
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, bytes, s->pool, s->astream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pool_free(void *p, void *ctx)
+{
+    dsea_server *s = static_cast<dsea_server *>(ctx);
+    if (p) cudaFreeAsync(p, s->astream);
+}
+
 int start_job(dsea_server *s, Job *j)
 {
     dsea_box_desc d = j->desc;
     d.pos = j->pos.data();
     d.vel = j->vel.empty() ? nullptr : j->vel.data();
-    int rc = dsea_box_create(&d, nullptr, s->stream, &j->box);
+    int rc = dsea_box_create(&d, &s->alloc, s->astream, &j->box);
     if (!rc) rc = dsea_register_kernel(j->box, DSEA_KERNEL_LJ_TS, 1, 1, &s->params);
     if (!rc) {
         j->pos.clear();
@@ -98,17 +128,54 @@ int start_job(dsea_server *s, Job *j)
     return rc;
 }
 
+// Read back a finished job on the admission stream and release it.
+void retire(dsea_server *s, Job *j)
+{
+    j->pos_out.resize(3 * j->desc.n_atoms);
+    j->vel_out.resize(3 * j->desc.n_atoms);
+    const int r2 = dsea::read_state(j->box, j->pos_out.data(), j->vel_out.data(), &j->obs);
+    finish(s, j, r2 ? r2 : 2);
+}
+
 void run(dsea_server *s)
 {
     cudaSetDevice(s->device);
-    std::vector<Job *> running;
+    std::vector<Job *> running, ready, retiring;
     while (true) {
+        // 1. launch the next segment over every resident box (the device then
+        //    runs while the host does steps 2 and 3)
+        const int n = (int)running.size();
+        std::vector<dsea_box *> boxes(n);
+        std::vector<int64_t> steps(n);
+        double work = 0;
+        int rc = DSEA_OK;
+        if (n > 0) {
+            for (int k = 0; k < n; ++k) {
+                boxes[k] = running[k]->box;
+                steps[k] = std::min<int64_t>(running[k]->remaining, s->segment);
+                work += (double)running[k]->desc.n_atoms * (double)steps[k];
+            }
+            rc = dsea::multi_prepare(s->mp, boxes.data(), steps.data(), n);
+            if (!rc) {
+                cudaEventRecord(s->ev0, s->stream);
+                rc = dsea::multi_enqueue(s->mp, boxes.data(), s->stream);
+                cudaEventRecord(s->ev1, s->stream);
+            }
+            if (!rc) dsea::multi_commit(boxes.data(), steps.data(), n);
+        }
+        // 2. jobs that finished in the previous segment: read back and release
+        for (Job *j : retiring) retire(s, j);
+        retiring.clear();
+        // 3. admit queued jobs while they fit; create and bin their boxes
         std::vector<Job *> admitted;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            while (!s->stop && s->queue.empty() && running.empty()) s->cv_work.wait(lk);
-            if (s->stop) break;
-            // admit in arrival order while the head of the queue fits the budget
+            while (!s->stop && s->queue.empty() && n == 0 && ready.empty()) s->cv_work.wait(lk);
+            if (s->stop) {
+                lk.unlock();
+                if (n > 0) cudaEventSynchronize(s->ev1);
+                break;
+            }
             while (!s->queue.empty() && s->used + s->queue.front()->bytes <= s->budget) {
                 Job *j = s->queue.front();
                 s->queue.pop_front();
@@ -119,64 +186,43 @@ void run(dsea_server *s)
             }
         }
         for (Job *j : admitted) {
-            const int rc = start_job(s, j);
-            if (rc) finish(s, j, rc);
-            else if (j->remaining == 0) {
-                j->pos_out.resize(3 * j->desc.n_atoms);
-                j->vel_out.resize(3 * j->desc.n_atoms);
-                const int r2 = dsea::read_state(j->box, j->pos_out.data(), j->vel_out.data(), &j->obs);
-                finish(s, j, r2 ? r2 : 2);
-            } else {
-                running.push_back(j);
-            }
+            const int jrc = start_job(s, j);
+            if (jrc) finish(s, j, jrc);
+            else if (j->remaining == 0) retire(s, j);
+            else ready.push_back(j);
         }
-        if (running.empty()) continue;
-        // one persistent launch over every resident box
-        const int n = (int)running.size();
-        std::vector<dsea_box *> boxes(n);
-        std::vector<int64_t> steps(n);
-        double work = 0;
-        for (int k = 0; k < n; ++k) {
-            boxes[k] = running[k]->box;
-            steps[k] = std::min<int64_t>(running[k]->remaining, s->segment);
-            work += (double)running[k]->desc.n_atoms * (double)steps[k];
-        }
-        int rc = dsea::multi_prepare(s->mp, boxes.data(), steps.data(), n);
-        if (!rc) {
-            cudaEventRecord(s->ev0, s->stream);
-            rc = dsea::multi_enqueue(s->mp, boxes.data(), s->stream);
-            cudaEventRecord(s->ev1, s->stream);
-        }
-        if (!rc) {
-            dsea::multi_commit(boxes.data(), steps.data(), n);
-            if (cudaEventSynchronize(s->ev1) != cudaSuccess) rc = DSEA_ERR_CUDA;
-        }
-        if (!rc) {
-            float ms = 0;
-            cudaEventElapsedTime(&ms, s->ev0, s->ev1);
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->busy_s += ms * 1e-3;
-            s->atom_steps += work;
-            s->launches += 1;
-        }
+        // 4. wait for the segment; account it and sort its boxes
         std::vector<Job *> still;
-        for (int k = 0; k < n; ++k) {
-            Job *j = running[k];
-            int jrc = rc ? rc : dsea_sync(j->box);
-            if (!jrc) j->remaining -= steps[k];
-            if (jrc) {
-                finish(s, j, jrc);
-            } else if (j->remaining == 0) {
-                j->pos_out.resize(3 * j->desc.n_atoms);
-                j->vel_out.resize(3 * j->desc.n_atoms);
-                const int r2 = dsea::read_state(j->box, j->pos_out.data(), j->vel_out.data(), &j->obs);
-                finish(s, j, r2 ? r2 : 2);
-            } else {
-                still.push_back(j);
+        if (n > 0) {
+            if (!rc && cudaEventSynchronize(s->ev1) != cudaSuccess) rc = DSEA_ERR_CUDA;
+            if (!rc) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->busy_s += ms * 1e-3;
+                s->atom_steps += work;
+                s->launches += 1;
             }
+            for (int k = 0; k < n; ++k) {
+                Job *j = running[k];
+                int jrc = rc ? rc : dsea_sync(j->box);
+                if (!jrc) j->remaining -= steps[k];
+                if (jrc) finish(s, j, jrc);
+                else if (j->remaining == 0) retiring.push_back(j);   // read back during the next segment
+                else still.push_back(j);
+            }
+        }
+        // 5. newly binned boxes join the next segment, after their binning
+        if (!ready.empty()) {
+            cudaEventRecord(s->ev_ready, s->astream);
+            cudaStreamWaitEvent(s->stream, s->ev_ready, 0);
+            still.insert(still.end(), ready.begin(), ready.end());
+            ready.clear();
         }
         running.swap(still);
     }
+    for (Job *j : retiring) retire(s, j);
+    for (Job *j : ready) finish(s, j, DSEA_ERR_STATE);
     for (Job *j : running) finish(s, j, DSEA_ERR_STATE);
 }
 
@@ -201,11 +247,39 @@ int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int s
     s->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&s->device);
     s->t0 = std::chrono::steady_clock::now();
-    if (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess) {
+    bool ok = true;
+    if (!s->stream) {   // no stream given: a non-blocking one of the server's own
+        ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
+        s->own_stream = ok;
+    }
+    ok = ok && cudaStreamCreateWithFlags(&s->astream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreate(&s->ev0) == cudaSuccess && cudaEventCreate(&s->ev1) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_ready, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess;
+        if (ok) {   // keep freed memory in the pool for the next jobs
+            uint64_t keep = UINT64_MAX;
+            ok = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess;
+        }
+    }
+    if (!ok) {
         cudaGetLastError();
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        if (s->ev_ready) cudaEventDestroy(s->ev_ready);
+        if (s->ev1) cudaEventDestroy(s->ev1);
+        if (s->ev0) cudaEventDestroy(s->ev0);
+        if (s->astream) cudaStreamDestroy(s->astream);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
         delete s;
         return DSEA_ERR_CUDA;
     }
+    s->alloc.alloc = pool_alloc;
+    s->alloc.free = pool_free;
+    s->alloc.ctx = s;
     s->worker = std::thread(run, s);
     *out = s;
     return DSEA_OK;
@@ -317,9 +391,15 @@ int dsea_server_destroy(dsea_server *s)
         if (kv.second->box) dsea_box_destroy(kv.second->box);
         delete kv.second;
     }
+    cudaStreamSynchronize(s->stream);
+    cudaStreamSynchronize(s->astream);
     dsea::multi_free(s->mp);
+    cudaMemPoolDestroy(s->pool);
     cudaEventDestroy(s->ev0);
     cudaEventDestroy(s->ev1);
+    cudaEventDestroy(s->ev_ready);
+    cudaStreamDestroy(s->astream);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
     return DSEA_OK;
 }

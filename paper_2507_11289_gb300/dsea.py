@@ -38,6 +38,9 @@ BOUNDARY_MIRROR = 1
 SCHED_STEPWISE = 1
 DEBUG_WITHHOLD_SLICE = 1
 DEBUG_WAIT_LIMIT_NS = 2
+PROBE_FP32 = 0
+PROBE_FP32X2 = 1
+PROBE_FP64 = 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -119,6 +122,7 @@ _SIGS = {
     "dsea_dataset_destroy": (_I, [_P]),
     "dsea_dataset_plan": (_I, [_I, _I, _I, _I, _I64, _I64, _P, _P, _P]),
     "dsea_example_heat1d": (_I, [_P, _I, _I64, _P, _P, ctypes.c_size_t, _P]),
+    "dsea_probe_peak": (_I, [_I, _P, ctypes.POINTER(_D)]),
 }
 
 _lib = None
@@ -539,3 +543,10 @@ class Dataset:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def probe_peak(kind: int = PROBE_FP32, stream=None) -> float:
+    """dsea_probe_peak: the measured FMA rate of this GPU in TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load().dsea_probe_peak(int(kind), _stream_handle(stream), ctypes.byref(out)), "dsea_probe_peak")
+    return out.value

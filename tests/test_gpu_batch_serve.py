@@ -126,7 +126,7 @@ def test_torch_allocator_owns_box_memory():
 
 
 def test_autotune_choice_does_not_leak_across_densities():
-    """The autotuner caches a unit shape per size class.  A dilute box and a
+    """The autotuner caches a unit shape per size class.  A sparser box and a
     dense one with the same cells per axis and the same cell capacity are
     different classes (mean atoms per cell), and so are a 17^3-cell box and
     the 43^3-cell 1M-atom box at the same density (total cells): tuning the
@@ -138,7 +138,7 @@ def test_autotune_choice_does_not_leak_across_densities():
 import json
 from paper_2507_11289_gb300 import dsea, inputs
 out = {}
-for name, n_i, rho in (("dilute", 10, 0.05), ("dense", 25, 0.8), ("big", 64, 0.8)):
+for name, n_i, rho in (("dilute", 22, 0.55), ("dense", 25, 0.8), ("big", 64, 0.8)):
     pos, box = inputs.fcc_lattice(n_i, rho)
     vel = inputs.maxwell_boltzmann(len(pos), 1.0, 3)
     with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:

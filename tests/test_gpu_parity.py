@@ -314,17 +314,19 @@ def _sparse_gas(n, box, dmin, seed):
 
 
 @pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
-@pytest.mark.parametrize("n", [240, 864])
+@pytest.mark.parametrize("n", [60, 240, 864])
 def test_sparse_gas_pairs_at_every_angle(precision, n):
-    """About one (four) atoms per cell: pairs reach the cutoff across faces,
-    edges and corners in every direction.  With four, the mixed form prunes
-    its lists to the neighbours near the small box its home atoms span; with
-    one, a home cell's short list is kept whole."""
-    box = np.array([15.6, 15.6, 15.6])                # 6 cells of 2.6 per axis
+    """Sparse gases (rho 0.016, 0.063 and 0.23): the cells grow to 3.12 (five
+    per axis, the most that keeps them within 1.5 rc), so about half an atom,
+    two and seven atoms share a cell; pairs reach the cutoff across faces,
+    edges and corners in every direction, and the mixed form prunes its lists
+    to the neighbours near the box its home atoms span (a lone atom's short
+    list is kept whole)."""
+    box = np.array([15.6, 15.6, 15.6])
     pos = _sparse_gas(n, box, 0.95, seed=41)
     Fo, Uo, Wo = oracle.forces(pos, box, RC, "brute")
     with dsea.Box(pos, None, box, precision=precision) as b:
-        assert b.info()["cells"] == [6, 6, 6]
+        assert b.info()["cells"] == [5, 5, 5]
         Fg = b.forces()
         ob = b.observables()
     tol = 1e-12 if precision == dsea.FP64 else 2e-6

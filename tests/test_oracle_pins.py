@@ -244,3 +244,19 @@ def test_melted_state_is_liquid_like(melted_4k):
     frms = np.sqrt((F ** 2).sum(1).mean())
     assert 10 < frms < 60          # far from the F = 0 lattice
     assert -6.0 < U / len(p) < -3.0
+
+
+def test_cell_list_does_not_depend_on_thread_count():
+    """The OpenMP force loop gives the same bits with one thread as with all
+    cores (per-atom sums, and U, W summed afterwards in atom order)."""
+    pos, vel, box = inputs.SMALL_4K.state()
+    pos = inputs.jitter(pos, box, 0.15, 77)
+    n_all = oracle.set_threads(0)
+    try:
+        oracle.set_threads(1)
+        F1, U1, W1 = oracle.forces(pos, box, RC, "cells")
+        oracle.set_threads(n_all)
+        Fn, Un, Wn = oracle.forces(pos, box, RC, "cells")
+    finally:
+        oracle.set_threads(n_all)
+    assert np.array_equal(F1, Fn) and U1 == Un and W1 == Wn
