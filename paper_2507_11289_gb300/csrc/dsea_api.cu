@@ -305,7 +305,7 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     // edge >= rc, so every pair within rc is still met exactly once per atom.
     const double vol_box = L[0] * L[1] * L[2];
     const double rho = vol_box > 0.0 ? (double)n_atoms / vol_box : 0.0;
-    const double edge = rho > 0.0 ? std::min(1.5 * p.rc, std::max(p.rc, std::cbrt(8.0 / rho))) : 1.5 * p.rc;
+    const double edge = rho > 0.0 ? std::min(1.5 * p.rc, std::max(p.rc, std::cbrt(12.0 / rho))) : 1.5 * p.rc;
     auto cells_along = [&](double len) {   // edge near `edge`, within [rc, 1.5 rc]; at least 3 cells
         const int n_max = (int)std::floor(len / p.rc);
         int n = std::max((int)std::floor(len / edge), (int)std::ceil(len / (1.5 * p.rc)));
@@ -419,6 +419,7 @@ const char *dsea_status_string(int s)
 int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, void *cuda_stream,
                     dsea_box **out)
 {
+    NvtxRange nvtx_range("dsea_box_create");
     if (!desc || !out || desc->n_atoms < 0 || desc->n_slices < 0) return DSEA_ERR_INVALID_ARG;
     if (desc->n_atoms > 0 && !desc->pos) return DSEA_ERR_INVALID_ARG;
     if (desc->n_atoms >= (int64_t)1 << 31) return DSEA_ERR_INVALID_ARG;
@@ -461,6 +462,7 @@ int dsea_box_create(const dsea_box_desc *desc, const dsea_allocator *allocator, 
 
 int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_params *params)
 {
+    NvtxRange nvtx_range("dsea_register_kernel");
     if (!b) return DSEA_ERR_INVALID_ARG;
     if (b->registered) return DSEA_ERR_STATE;
     if (kind != DSEA_KERNEL_LJ_TS || o_in != 1 || o_out != 1) return DSEA_ERR_INVALID_ARG;
@@ -535,6 +537,7 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
 
 int dsea_advance(dsea_box *b, int64_t n_steps)
 {
+    NvtxRange nvtx_range("dsea_advance");
     if (!b || n_steps < 0) return DSEA_ERR_INVALID_ARG;
     if (!b->registered) return DSEA_ERR_STATE;
     if (b->latched) return b->latched;
@@ -550,6 +553,7 @@ int dsea_sync(dsea_box *b)
 
 int dsea_read_positions(dsea_box *b, double *out, int64_t n)
 {
+    NvtxRange nvtx_range("dsea_read_positions");
     int rc = read_array(b, out, n);
     if (rc) return rc;
     CU(cudaMemcpyAsync(out, b->hb.out_r, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
@@ -559,6 +563,7 @@ int dsea_read_positions(dsea_box *b, double *out, int64_t n)
 
 int dsea_read_velocities(dsea_box *b, double *out, int64_t n)
 {
+    NvtxRange nvtx_range("dsea_read_velocities");
     int rc = read_array(b, out, n);
     if (rc) return rc;
     CU(cudaMemcpyAsync(out, b->hb.out_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
@@ -568,6 +573,7 @@ int dsea_read_velocities(dsea_box *b, double *out, int64_t n)
 
 int dsea_read_forces(dsea_box *b, double *out, int64_t n)
 {
+    NvtxRange nvtx_range("dsea_read_forces");
     int rc = read_array(b, out, n);
     if (rc) return rc;
     CU(cudaMemcpyAsync(out, b->hb.out_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream));
@@ -577,6 +583,7 @@ int dsea_read_forces(dsea_box *b, double *out, int64_t n)
 
 int dsea_read_observables(dsea_box *b, dsea_observables *out)
 {
+    NvtxRange nvtx_range("dsea_read_observables");
     if (!b || !out) return DSEA_ERR_INVALID_ARG;
     if (!b->registered) return DSEA_ERR_STATE;
     int rc = ensure_outputs(b);
@@ -590,6 +597,7 @@ int dsea_read_observables(dsea_box *b, dsea_observables *out)
 
 int dsea_read_profiles(dsea_box *b, double *U, double *W, double *KE, int64_t *N, int n)
 {
+    NvtxRange nvtx_range("dsea_read_profiles");
     if (!b) return DSEA_ERR_INVALID_ARG;
     if (!b->registered) return DSEA_ERR_STATE;
     const BoxDev &hb = b->hb;
@@ -643,6 +651,7 @@ int dsea_box_get_info(const dsea_box *b, dsea_box_info *o)
 
 int dsea_box_destroy(dsea_box *b)
 {
+    NvtxRange nvtx_range("dsea_box_destroy");
     if (!b) return DSEA_ERR_INVALID_ARG;
     if (b->registered) cudaStreamSynchronize(b->stream);
     dev_free_all(b);
@@ -693,6 +702,7 @@ int dsea_batch_create(dsea_box *const *boxes, int n, dsea_batch **out)
 
 int dsea_batch_advance(dsea_batch *bt, const int64_t *steps)
 {
+    NvtxRange nvtx_range("dsea_batch_advance");
     if (!bt || !steps) return DSEA_ERR_INVALID_ARG;
     const int n = (int)bt->boxes.size();
     int64_t smax = 0;
@@ -767,6 +777,7 @@ int dsea_batch_destroy(dsea_batch *bt)
 
 int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
 {
+    NvtxRange nvtx_range("dsea_autotune");
     if (!b || trial_steps <= 0) return DSEA_ERR_INVALID_ARG;
     if (!b->registered) return DSEA_ERR_STATE;
     int rc = check_device_error(b);

@@ -20,7 +20,7 @@
 #include <new>
 #include <vector>
 
-#include "dsea.h"
+#include "dsea_host.h"
 
 struct dsea_dataset {
     int n_slices = 0;
@@ -177,6 +177,7 @@ int dsea_dataset_register(dsea_dataset *d, dsea_slice_fn fn, void *user)
 
 int dsea_dataset_run(dsea_dataset *d, int64_t n_steps)
 {
+    NvtxRange nvtx_range("dsea_dataset_run");
     if (!d || n_steps < 0) return DSEA_ERR_INVALID_ARG;
     if (!d->fn) return DSEA_ERR_STATE;
     if (n_steps == 0) return DSEA_OK;

@@ -5,9 +5,21 @@
 #include "dsea.h"
 #include "dsea_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <map>
 #include <utility>
 #include <vector>
+
+// A named NVTX range over a scope of host code (the library's calls and the
+// server's phases show up by name on a profiler's timeline; without a tool
+// attached a range costs a call through a null hook).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct dsea_box {
     int device = 0;

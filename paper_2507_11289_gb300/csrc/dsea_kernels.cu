@@ -727,11 +727,16 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             int *myq = reinterpret_cast<int *>(smem + Ly.queue) + warp * 32 * kQueueDepth + lane;
             int nq = 0;
             // FP32 pre-test.  The FP32 coordinates (|x| <= E, the unit's extent)
-            // carry an error of at most E 2^-24 each, so near the cutoff (|d| <= rc)
-            // the FP32 r2 differs from the FP64 one by less than
-            // (6 rc E + 3 rc^2) 2^-24; four times that is the band.  Outside
-            // (band, rc2 - band) and above rc2 + band the FP64 test would decide
-            // the same way; in between it decides.
+            // carry an error of at most E 2^-24 each and the FP32 subtraction
+            // adds at most |d| 2^-24, so near the cutoff (|d_k| <= r <= rc) each
+            // component is off by at most (2E + rc) 2^-24; squaring and summing
+            // (sum |d_k| <= sqrt(3) r) gives 2 sqrt(3) rc (2E + rc) 2^-24, and the
+            // three roundings of r2 add 3 rc^2 2^-24: to first order the FP32 r2
+            // is within (6.93 rc E + 6.47 rc^2) 2^-24 of the FP64 one.  The band
+            // is 4 (6 rc E + 3 rc^2) 2^-24 = (24 rc E + 12 rc^2) 2^-24: more than
+            // 1.8 times that at any E, three times at the extents of a unit (E
+            // of three cells or more).  Outside (band, rc2 - band) and above rc2 + band
+            // the FP64 test would decide the same way; in between it decides.
             const float xif = act ? s_xf[is] : 0.f, yif = act ? s_yf[is] : 0.f, zif = act ? s_zf[is] : 0.f;
             auto drain = [&]() {
                 const int nmax = __reduce_max_sync(kFull, nq);
@@ -1422,12 +1427,6 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, O
         const int hx = v.hx, hy = v.hy, hz = v.hz;
         int total = 0;
         const NbrCell c = nbr_cell(B, (int)(s_abs & 1), (unsigned)(s_abs + 1), hx, hy, hz, lane, total);
-        if (__shfl_sync(kFull, c.n_s + c.n_a, 0) == 0) {   // an empty home cell only publishes its count
-            if (INTEGRATE && lane == 0)
-                B.cnt[(int)(s_abs & 1) ^ 1][c.gc] = (unsigned long long)(unsigned)(s_abs + 2) << 32;
-            __syncwarp();
-            return;
-        }
         build_window(B, (int)(s_abs & 1), c, total, 0, lane, wa);
         if (lane == 0) {
             wa.n_home = c.n_s + c.n_a;

@@ -62,6 +62,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
                                    const double *box, double rc, int precision, double *forces_dev,
                                    double *obs3_dev, void *cuda_stream)
 {
+    NvtxRange nvtx_range("dsea_forces_noalloc");
     if (n_atoms < 0 || !box || (n_atoms > 0 && (!pos_dev || !forces_dev))) return DSEA_ERR_INVALID_ARG;
     if (n_atoms >= ((int64_t)1 << 31)) return DSEA_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)cuda_stream;

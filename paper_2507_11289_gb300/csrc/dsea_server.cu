@@ -144,6 +144,7 @@ void run(dsea_server *s)
     while (true) {
         // 1. launch the next segment over every resident box (the device then
         //    runs while the host does steps 2 and 3)
+        NvtxRange nvtx_cycle("server cycle");
         const int n = (int)running.size();
         std::vector<dsea_box *> boxes(n);
         std::vector<int64_t> steps(n);
@@ -164,7 +165,10 @@ void run(dsea_server *s)
             if (!rc) dsea::multi_commit(boxes.data(), steps.data(), n);
         }
         // 2. jobs that finished in the previous segment: read back and release
-        for (Job *j : retiring) retire(s, j);
+        if (!retiring.empty()) {
+            NvtxRange r("server read-back");
+            for (Job *j : retiring) retire(s, j);
+        }
         retiring.clear();
         // 3. admit queued jobs while they fit; create and bin their boxes
         std::vector<Job *> admitted;
@@ -185,11 +189,14 @@ void run(dsea_server *s)
                 admitted.push_back(j);
             }
         }
-        for (Job *j : admitted) {
-            const int jrc = start_job(s, j);
-            if (jrc) finish(s, j, jrc);
-            else if (j->remaining == 0) retire(s, j);
-            else ready.push_back(j);
+        if (!admitted.empty()) {
+            NvtxRange r("server admission");
+            for (Job *j : admitted) {
+                const int jrc = start_job(s, j);
+                if (jrc) finish(s, j, jrc);
+                else if (j->remaining == 0) retire(s, j);
+                else ready.push_back(j);
+            }
         }
         // 4. wait for the segment; account it and sort its boxes
         std::vector<Job *> still;

@@ -127,11 +127,11 @@ def test_torch_allocator_owns_box_memory():
 
 def test_autotune_choice_does_not_leak_across_densities():
     """The autotuner caches a unit shape per size class.  A sparser box and a
-    dense one with the same cells per axis and the same cell capacity are
-    different classes (mean atoms per cell), and so are a 17^3-cell box and
-    the 43^3-cell 1M-atom box at the same density (total cells): tuning the
-    first of each pair leaves the second on the default shape.  Run in a
-    fresh process: the cache lives as long as the library."""
+    dense one of about the same edge are different classes (mean atoms per
+    cell; below rho 0.77 the cells are also larger), and so are a 17^3-cell
+    box and the 43^3-cell 1M-atom box at the same density (total cells):
+    tuning the first of each pair leaves the second on the default shape.  Run
+    in a fresh process: the cache lives as long as the library."""
     import subprocess
     import sys
     code = """
@@ -157,7 +157,6 @@ print(json.dumps(out))
     assert r.returncode == 0, r.stderr
     out = json.loads(r.stdout.strip().splitlines()[-1])
     d, e, g = out["dilute"], out["dense"], out["big"]
-    assert d["cells"] == e["cells"] and d["cap"] == e["cap"]       # the same key without density
     assert e["tile"] == [2, 4], out                                # the mixed default, untouched
     assert g["cap"] == e["cap"] and min(g["cells"][1:]) >= 16 and min(e["cells"][1:]) >= 16
     assert g["tile"] == [2, 4], out                                # not the 17^3 box's choice

@@ -170,7 +170,7 @@ def test_smallest_box_and_ragged_units():
         assert b.info()["cells"] == [3, 3, 3]
         b.advance(20)
         assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
-    pos, box = inputs.fcc_lattice(10, 0.55)          # 19.4 edge: 7 cells
+    pos, box = inputs.fcc_lattice(11, 0.8)           # 18.8 edge: 7 cells
     pos = inputs.jitter(pos, box, 0.1, 5)
     vel = inputs.maxwell_boltzmann(len(pos), 1.0, 6)
     ro, _, _, _ = oracle.run(pos, vel, box, steps=20)

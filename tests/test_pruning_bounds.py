@@ -46,6 +46,22 @@ def band(E):
     return 4.0 * (6.0 * np.sqrt(RC2) * E + 3.0 * RC2) * 2.0 ** -24
 
 
+def fp32_r2_error_bound(E):
+    """First-order bound on |FP32 r^2 - FP64 r^2| near the cutoff: coordinate
+    roundings (E 2^-24 each) and the subtraction's (rc 2^-24) per component,
+    squared and summed (sum |d_k| <= sqrt(3) rc), plus three roundings of
+    r^2 (3 rc^2 2^-24)."""
+    rc = np.sqrt(RC2)
+    return (2.0 * np.sqrt(3.0) * rc * (2.0 * E + rc) + 3.0 * RC2) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("E", [0.0, 1.0, 7.5, 15.0, 40.0, 1000.0])
+def test_fp64_form_band_covers_the_error_bound(E):
+    assert band(E) >= 1.8 * fp32_r2_error_bound(E)
+    if E >= 7.5:                        # a unit spans three cells of edge >= rc
+        assert band(E) >= 3.0 * fp32_r2_error_bound(E)
+
+
 @pytest.mark.parametrize("E,seed", [(15.0, 5), (40.0, 6), (1000.0, 7)])
 def test_fp64_form_fp32_decisions_agree_with_fp64(E, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -63,6 +79,8 @@ def test_fp64_form_fp32_decisions_agree_with_fp64(E, seed):
     r2 = ((xi - xj) ** 2).sum(1)                                # the FP64 decision
     in64 = (r2 <= RC2) & (r2 > 0.0)
     r2f = f32_r2((xi - corner).astype(F32) - (xj - corner).astype(F32))
+    # the stated bound holds on every sample (and the band is wider still)
+    assert np.abs(r2f.astype(np.float64) - r2).max() <= fp32_r2_error_bound(E)
     sure_out = r2f > hi_out
     sure_in = (r2f < lo_in) & (r2f > tiny)
     assert not np.any(sure_out & in64)
