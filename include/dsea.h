@@ -288,8 +288,8 @@ int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev, int64_t n_
  * fused multiply-adds (2 flops each); DSEA_PROBE_FP32X2: packed two-lane FP32
  * FMAs (fma.rn.f32x2, 4 flops each); DSEA_PROBE_FP64: FP64 FMAs.  8 CTAs of
  * 256 threads per SM, 8 independent chains per thread; *tflops receives the
- * counted flops over the CUDA-event time of one launch on `cuda_stream`
- * (after an untimed warm-up launch).  The call allocates a small device
+ * counted flops over the CUDA-event time of the fastest of three launches
+ * on `cuda_stream` (after an untimed warm-up launch).  The call allocates a small device
  * buffer, waits for the stream and returns DSEA_OK, DSEA_ERR_INVALID_ARG,
  * DSEA_ERR_NO_DEVICE or DSEA_ERR_CUDA. */
 #define DSEA_PROBE_FP32 0
