@@ -78,8 +78,9 @@ typedef struct {
     double dt;         /* timestep, tau */
     int precision;     /* DSEA_FP64 or DSEA_MIXED */
     int schedule;      /* DSEA_SCHED_RING or DSEA_SCHED_STEPWISE */
-    int tile_y;        /* home cells per work unit along y; 0 = automatic */
-    int tile_z;        /* home cells per work unit along z; 0 = automatic */
+    int tile_y;        /* home cells per work unit along y; tile_y = tile_z = 0:
+                          automatic (see below) */
+    int tile_z;        /* home cells per work unit along z */
     int cell_capacity; /* atom slots per cell; 0 = from the density */
     int ctas;          /* CTAs of a ring launch (one stage each in the FP64 form, one per
                           warp in the mixed form); 0 = all that fit */
@@ -89,6 +90,18 @@ typedef struct {
                            the slice's temperature after the previous step's scaling
                            (factor 1 at the first step) */
 } dsea_params;
+
+/* Automatic work-unit shape (tile_y = tile_z = 0).  A box takes, in order:
+ * the dsea_autotune choice cached for its size class; in the mixed form,
+ * where a unit is one warp's, the launch-filling shape of the box alone (the
+ * largest of 4x4, 3x3, 2x4, 2x2, 1x4, 1x2 home cells whose units per step
+ * reach twice the warp stages one launch keeps resident, 32 per SM; else
+ * 1x2); in the FP64 form 2 x 4.  Boxes on the automatic shape are re-shaped
+ * together when they share a launch: dsea_batch_create and each server
+ * launch apply the launch-filling rule to the units of all of them.  Only one
+ * of the two set: that side as given, the other 2 (y) or 4 (z).  A shape
+ * larger than the box, or whose stage does not fit a unit's shared memory,
+ * is shrunk (longer side first).  The shape never changes a result. */
 
 /* Boundary along x (the slicing axis).  y and z are always periodic. */
 #define DSEA_BOUNDARY_PERIODIC 0 /* minimum image along x as well */
@@ -196,8 +209,10 @@ int dsea_box_destroy(dsea_box *box);
 
 /* Group n boxes (same device, same stream, same precision, all registered)
  * so that one persistent launch advances all of them; the launch is captured
- * once in a CUDA graph per distinct step vector and replayed.  The boxes stay
- * owned by the caller and must outlive the batch. */
+ * once in a CUDA graph per distinct step vector and replayed.  Mixed-precision
+ * boxes on the automatic unit shape take the launch-filling shape of the
+ * whole batch (see dsea_params).  The boxes stay owned by the caller and must
+ * outlive the batch. */
 int dsea_batch_create(dsea_box *const *boxes, int n, dsea_batch **out);
 
 /* Advance box k by steps[k] >= 0 steps, all in one launch. */
@@ -216,12 +231,29 @@ int dsea_batch_destroy(dsea_batch *batch);
  * receives the parameters in effect. */
 int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);
 
+/* Choose one unit shape for every box of a batch: each candidate (the same
+ * list as dsea_autotune's) is applied to all boxes, shrunk per box where its
+ * cells or its shared-memory stage do not allow it, and the batch is timed
+ * over trial_steps steps in one dsea_batch_advance from snapshots of every
+ * box's state, which are restored after each trial.  The boxes keep the
+ * fastest shape; *tile_y, *tile_z (may be NULL) receive it.  Many boxes in
+ * one launch fill the GPU by themselves, so the batch's best shape is
+ * usually larger than what dsea_autotune picks for a small box alone.  The
+ * boxes leave the automatic shape; the lone-box cache is not changed.  Snapshots take device memory of the size of every
+ * box's state; DSEA_ERR_OOM if it is not there (the boxes are unchanged).
+ * The shape never changes a result.  Results: DSEA_OK, DSEA_ERR_INVALID_ARG
+ * (NULL batch, trial_steps <= 0), or a latched device error of a box. */
+int dsea_batch_autotune(dsea_batch *batch, int trial_steps, int *tile_y, int *tile_z);
+
 /* ---- serving ----------------------------------------------------------- */
 
 /* A continuous-batching server: jobs (boxes with a step count) are admitted
  * while their device state fits mem_budget_bytes, kept resident, and
  * advanced together in persistent launches of at most segment_steps steps;
- * jobs join and leave between launches.  A host thread drives the device. */
+ * jobs join and leave between launches.  A host thread drives the device.
+ * With tile_y = tile_z = 0 in params, each launch re-shapes the jobs present
+ * by the launch-filling rule (see dsea_params): small units while few jobs
+ * run, larger ones once they fill the GPU together. */
 int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int segment_steps,
                        void *cuda_stream, dsea_server **out);
 

@@ -145,6 +145,45 @@ bool apply_tile(BoxDev &hb, double mean_cap, int ty, int tz)
            dsea::max_unit_smem_bytes();
 }
 
+// The requested unit shape, or the largest one below it (shrinking the longer
+// side first) whose stage fits one unit's shared memory; false if not even one
+// cell's does.
+bool fit_tile(BoxDev &hb, double mean_cap, int ty, int tz)
+{
+    while (!apply_tile(hb, mean_cap, ty, tz)) {
+        if (ty == 1 && tz == 1) return false;
+        if (tz >= ty && tz > 1) --tz;
+        else --ty;
+    }
+    return true;
+}
+
+// Launch-filling unit shape of the mixed form, where a unit is one warp's: the
+// largest of these shapes whose units per step (summed over every box of the
+// launch) reach twice the warp stages the launch keeps resident (32 per SM:
+// 4 CTAs of 8 warps), else the smallest.  Below about two units per stage the
+// slice dependencies of the ring leave warps idle; above it a larger unit
+// gathers each neighbour cell for more home cells.  On batches of 1 to 512
+// boxes (3k to 11M atoms) the rule picks the fastest of the six shapes or
+// one within 1.5 % of it.
+constexpr int kFillShapes[][2] = {{4, 4}, {3, 3}, {2, 4}, {2, 2}, {1, 4}, {1, 2}};
+constexpr int kNumFillShapes = 6;
+
+int64_t units_with_tile(BoxDev hb, double mean_cap, int ty, int tz)
+{
+    if (!fit_tile(hb, mean_cap, ty, tz)) return 0;
+    return (int64_t)hb.n_slices * hb.units_per_slice;
+}
+
+template <class UnitsOf>
+int pick_filling_shape(UnitsOf units_of)
+{
+    const int64_t want = 2LL * num_sms() * 32;
+    for (int ci = 0; ci < kNumFillShapes; ++ci)
+        if (units_of(ci) >= want) return ci;
+    return kNumFillShapes - 1;
+}
+
 int upload_desc(dsea_box *b)
 {
     CU(cudaMemcpyAsync(b->db, &b->hb, sizeof(BoxDev), cudaMemcpyHostToDevice, b->stream));
@@ -281,6 +320,77 @@ TuneKey size_class(const int *nc, int cps, int cap, int precision, int64_t n_ato
     const int size = (int)std::floor(std::log2(std::max(cells, 1.0)));
     return TuneKey{occ, size, std::min(nc[1], 16), std::min(nc[2], 16), cps, cap, precision};
 }
+// A copy of the state buffers an advance reads (cell counts, IDs, positions,
+// velocities, pair records of the current parity) and the step counters, so
+// that timing trials leave a box as they found it.
+struct BoxSnapshot {
+    dsea_box *b = nullptr;
+    int parity = 0;
+    int64_t step0 = 0;
+    int sync0 = 0;
+    bool mixed = false;
+    size_t b_cnt = 0, b_id = 0, b_r = 0, b_v = 0, b_q = 0;
+    void *s_cnt = nullptr, *s_id = nullptr, *s_r = nullptr, *s_v = nullptr, *s_q = nullptr;
+
+    int save(dsea_box *box)
+    {
+        b = box;
+        const BoxDev &hb = b->hb;
+        parity = (int)(hb.step & 1);
+        step0 = hb.step;
+        sync0 = hb.w_is_sync;
+        mixed = hb.precision == DSEA_MIXED;
+        b_cnt = sizeof(unsigned long long) * 2 * hb.n_cells;
+        b_id = sizeof(int) * hb.n_slots;
+        b_r = sizeof(double) * 3 * hb.n_slots;
+        b_q = sizeof(float4) * hb.n_slots;
+        b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
+        const bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess &&
+                        (mixed || cudaMalloc(&s_id, b_id) == cudaSuccess) &&
+                        cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_v) == cudaSuccess &&
+                        (!mixed || cudaMalloc(&s_q, b_q) == cudaSuccess);
+        if (!ok) {
+            cudaGetLastError();
+            release();
+            return DSEA_ERR_OOM;
+        }
+        return copy(true);
+    }
+    // copies back and resets the step counters; the other parity's stale
+    // counts are zeroed so that they cannot match
+    int restore()
+    {
+        b->hb.step = step0;
+        b->hb.w_is_sync = sync0;
+        return copy(false);
+    }
+    void release()
+    {
+        for (void *q : {s_cnt, s_id, s_r, s_v, s_q})
+            if (q) cudaFree(q);
+        s_cnt = s_id = s_r = s_v = s_q = nullptr;
+    }
+    ~BoxSnapshot() { release(); }
+
+  private:
+    int copy(bool save)
+    {
+        BoxDev &hb = b->hb;
+        const int p = parity;
+        auto c = [&](void *snap, void *live, size_t bytes) {
+            return save ? cudaMemcpyAsync(snap, live, bytes, cudaMemcpyDeviceToDevice, b->stream)
+                        : cudaMemcpyAsync(live, snap, bytes, cudaMemcpyDeviceToDevice, b->stream);
+        };
+        cudaError_t e = c(s_cnt, hb.cnt[p], b_cnt);
+        if (e == cudaSuccess && s_id) e = c(s_id, hb.id[p], b_id);
+        if (e == cudaSuccess) e = c(s_r, hb.r[p], b_r);
+        if (e == cudaSuccess) e = c(s_v, mixed ? (void *)hb.vf[p] : (void *)hb.v[p], b_v);
+        if (e == cudaSuccess && s_q) e = c(s_q, hb.q[p], b_q);
+        if (e == cudaSuccess && !save) e = cudaMemsetAsync(hb.cnt[p ^ 1], 0, b_cnt, b->stream);
+        return map_cuda(e);
+    }
+};
+
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 
@@ -362,26 +472,28 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
     hb.w_is_sync = 1;
     hb.withhold_slice = -1;
     hb.wait_limit_ns = 5000000000LL;   // 5 s
-    // work-unit shape: requested, cached by the autotuner, or the default of
-    // 2 x 4 home cells (per warp in the mixed form, per CTA in the FP64 form,
-    // where it keeps two CTAs' staging in one SM's shared memory)
+    // work-unit shape: requested, cached by the autotuner, or by default the
+    // launch-filling shape of the box alone (mixed form, a warp's unit) or
+    // 2 x 4 home cells (FP64 form, a CTA's unit: two CTAs' staging fit one
+    // SM's shared memory)
     int ty = p.tile_y, tz = p.tile_z;
-    if (ty == 0 || tz == 0) {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (ty == 0 && tz == 0) {
+        std::unique_lock<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(size_class(hb.nc, cps, cap, p.precision, n_atoms));
         if (it != g_tune_cache.end()) {
             ty = it->second.first;
             tz = it->second.second;
-        } else {
-            ty = ty ? ty : 2;
-            tz = tz ? tz : 4;
+        } else if (p.precision == DSEA_MIXED) {
+            lk.unlock();
+            const int ci = pick_filling_shape(
+                [&](int c) { return units_with_tile(hb, mean_cap, kFillShapes[c][0], kFillShapes[c][1]); });
+            ty = kFillShapes[ci][0];
+            tz = kFillShapes[ci][1];
         }
     }
-    while (!apply_tile(hb, mean_cap, ty, tz)) {
-        if (ty == 1 && tz == 1) return DSEA_ERR_INVALID_ARG;   // one cell's stage does not fit
-        if (tz >= ty && tz > 1) --tz;
-        else --ty;
-    }
+    ty = ty ? ty : 2;
+    tz = tz ? tz : 4;
+    if (!fit_tile(hb, mean_cap, ty, tz)) return DSEA_ERR_INVALID_ARG;   // one cell's stage does not fit
     p.tile_y = hb.tile_y;
     p.tile_z = hb.tile_z;
     p.cell_capacity = cap;
@@ -471,8 +583,10 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
     if (!(p.temperature >= 0.0) || !std::isfinite(p.temperature)) return DSEA_ERR_INVALID_ARG;
     CU(cudaSetDevice(b->device));
     BoxDev &hb = b->hb;
+    const bool tile_auto = p.tile_y == 0 && p.tile_z == 0;
     int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
     if (rc0) return rc0;
+    b->tile_auto = tile_auto;
     hb.walls_x = b->walls_x;
     const int n_s = hb.n_slices;
     b->params = p;
@@ -688,6 +802,7 @@ int dsea_batch_create(dsea_box *const *boxes, int n, dsea_batch **out)
     dsea_batch *bt = new (std::nothrow) dsea_batch();
     if (!bt) return DSEA_ERR_OOM;
     bt->boxes.assign(boxes, boxes + n);
+    dsea::retile_for_launch(bt->boxes.data(), n);   // boxes on the automatic shape fill the launch together
     bt->stream = boxes[0]->stream;
     bt->precision = boxes[0]->hb.precision;
     if (cudaEventCreateWithFlags(&bt->done_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -722,12 +837,13 @@ int dsea_batch_advance(dsea_batch *bt, const int64_t *steps)
     }
     int rc = dsea::multi_prepare(bt->mp, bt->boxes.data(), steps, n);
     if (rc) return rc;
-    std::vector<int64_t> key(2 * n + 1);
+    std::vector<int64_t> key(2 * n + 2);
     for (int k = 0; k < n; ++k) {
         key[k] = bt->mp.order[k];
         key[n + k] = steps[bt->mp.order[k]];
     }
     key[2 * n] = (int64_t)bt->mp.smem;
+    key[2 * n + 1] = bt->mp.total;   // the grid is sized by the units of the whole run
     auto it = bt->graphs.find(key);
     if (it == bt->graphs.end()) {
         cudaStream_t st = bt->stream;
@@ -795,47 +911,9 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         }
     }
     if (!cached) {
-        // snapshot the current state buffer so the trials leave the box unchanged
-        const int p = (int)(hb.step & 1);
-        const int64_t step0 = hb.step;
-        const int sync0 = hb.w_is_sync;
-        const size_t b_cnt = sizeof(unsigned long long) * 2 * hb.n_cells, b_id = sizeof(int) * hb.n_slots,
-                     b_r = sizeof(double) * 3 * hb.n_slots, b_q = sizeof(float4) * hb.n_slots;
-        const bool mixed = hb.precision == DSEA_MIXED;
-        const size_t b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
-        void *s_cnt = nullptr, *s_id = nullptr, *s_r = nullptr, *s_v = nullptr, *s_q = nullptr;
-        bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess &&
-                  (mixed || cudaMalloc(&s_id, b_id) == cudaSuccess) &&
-                  cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_v) == cudaSuccess &&
-                  (!mixed || cudaMalloc(&s_q, b_q) == cudaSuccess);
-        auto release = [&]() {
-            cudaFree(s_cnt); cudaFree(s_r); cudaFree(s_v);
-            if (s_id) cudaFree(s_id);
-            if (s_q) cudaFree(s_q);
-        };
-        if (!ok) {
-            cudaGetLastError();
-            release();
-            return DSEA_ERR_OOM;
-        }
-        auto copy = [&](bool save) -> cudaError_t {
-            auto c = [&](void *snap, void *live, size_t bytes) {
-                return save ? cudaMemcpyAsync(snap, live, bytes, cudaMemcpyDeviceToDevice, b->stream)
-                            : cudaMemcpyAsync(live, snap, bytes, cudaMemcpyDeviceToDevice, b->stream);
-            };
-            cudaError_t e = c(s_cnt, hb.cnt[p], b_cnt);
-            if (e == cudaSuccess && s_id) e = c(s_id, hb.id[p], b_id);
-            if (e == cudaSuccess) e = c(s_r, hb.r[p], b_r);
-            if (e == cudaSuccess) e = c(s_v, mixed ? (void *)hb.vf[p] : (void *)hb.v[p], b_v);
-            if (e == cudaSuccess && s_q) e = c(s_q, hb.q[p], b_q);
-            if (e == cudaSuccess && !save)   // stale counts of the other buffer must not match
-                e = cudaMemsetAsync(hb.cnt[p ^ 1], 0, b_cnt, b->stream);
-            return e;
-        };
-        if (copy(true) != cudaSuccess) {
-            release();
-            return DSEA_ERR_CUDA;
-        }
+        BoxSnapshot snap;
+        rc = snap.save(b);
+        if (rc) return rc;
         // candidate unit shapes: mixed units are one warp's, FP64 units one CTA's
         static const int cand_mixed[][2] = {{1, 2}, {2, 2}, {1, 4}, {2, 4}, {3, 3}, {4, 4}};
         static const int cand_f64[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
@@ -863,9 +941,8 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
             if (!rc) rc = check_device_error(b);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            hb.step = step0;
-            hb.w_is_sync = sync0;
-            copy(false);
+            const int rrc = snap.restore();
+            if (!rc) rc = rrc;
             if (rc) break;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -876,7 +953,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaStreamSynchronize(b->stream);
-        release();
+        snap.release();
         hb = saved;
         if (rc) return rc;
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -885,8 +962,86 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
     apply_tile(hb, b->mean_cap, best.first, best.second);
     b->params.tile_y = hb.tile_y;
     b->params.tile_z = hb.tile_z;
+    b->tile_auto = false;
     b->outputs_valid = false;
     if (chosen) *chosen = b->params;
+    return DSEA_OK;
+}
+
+int dsea_batch_autotune(dsea_batch *bt, int trial_steps, int *tile_y, int *tile_z)
+{
+    NvtxRange nvtx_range("dsea_batch_autotune");
+    if (!bt || trial_steps <= 0) return DSEA_ERR_INVALID_ARG;
+    const int n = (int)bt->boxes.size();
+    for (dsea_box *b : bt->boxes) {
+        const int rc = check_device_error(b);
+        if (rc) return rc;
+    }
+    std::vector<BoxSnapshot> snaps(n);
+    std::vector<BoxDev> saved(n);
+    for (int k = 0; k < n; ++k) {
+        const int rc = snaps[k].save(bt->boxes[k]);
+        if (rc) return rc;
+        saved[k] = bt->boxes[k]->hb;
+    }
+    // the same candidates as a lone box's; every box takes the candidate,
+    // shrunk where its cells or its stage do not allow it
+    static const int cand_mixed[][2] = {{1, 2}, {2, 2}, {1, 4}, {2, 4}, {3, 3}, {4, 4}};
+    static const int cand_f64[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
+    const bool mixed = bt->precision == DSEA_MIXED;
+    const int n_cand = mixed ? 6 : 8;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return DSEA_ERR_CUDA;
+    }
+    std::vector<int64_t> warm(n, 1), trial(n, trial_steps);
+    std::pair<int, int> best{0, 0};
+    float best_ms = 1e30f;
+    int rc = DSEA_OK;
+    for (int ci = 0; ci < n_cand && !rc; ++ci) {
+        const int *c = mixed ? cand_mixed[ci] : cand_f64[ci];
+        for (int k = 0; k < n && !rc; ++k) {
+            dsea_box *b = bt->boxes[k];
+            b->hb = saved[k];
+            if (!fit_tile(b->hb, b->mean_cap, c[0], c[1])) rc = DSEA_ERR_INVALID_ARG;
+        }
+        if (rc) break;
+        rc = dsea_batch_advance(bt, warm.data());
+        if (!rc) rc = map_cuda(cudaEventRecord(e0, bt->stream));
+        if (!rc) rc = dsea_batch_advance(bt, trial.data());
+        if (!rc) rc = map_cuda(cudaEventRecord(e1, bt->stream));
+        for (int k = 0; k < n && !rc; ++k) rc = check_device_error(bt->boxes[k]);
+        float ms = 0;
+        if (!rc) rc = map_cuda(cudaEventElapsedTime(&ms, e0, e1));
+        for (int k = 0; k < n; ++k) {
+            const int rrc = snaps[k].restore();
+            if (!rc) rc = rrc;
+        }
+        if (!rc && ms < best_ms) {
+            best_ms = ms;
+            best = {c[0], c[1]};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(bt->stream);
+    for (int k = 0; k < n; ++k) {
+        dsea_box *b = bt->boxes[k];
+        b->hb = saved[k];
+        if (!rc) {
+            fit_tile(b->hb, b->mean_cap, best.first, best.second);
+            b->tile_auto = false;
+        }
+        b->params.tile_y = b->hb.tile_y;
+        b->params.tile_z = b->hb.tile_z;
+        b->outputs_valid = false;
+        snaps[k].release();
+    }
+    if (rc) return rc;
+    if (tile_y) *tile_y = best.first;
+    if (tile_z) *tile_z = best.second;
     return DSEA_OK;
 }
 
@@ -912,6 +1067,35 @@ int dsea_ring_order(int n_slices, int units_per_slice, int64_t n_steps, int64_t 
 // ---- shared host machinery (used by batches and the server) -------------------
 
 namespace dsea {
+
+void retile_for_launch(dsea_box *const *boxes, int n)
+{
+    int64_t fixed = 0;
+    bool any = false;
+    for (int k = 0; k < n; ++k) {
+        const dsea_box *b = boxes[k];
+        if (b->tile_auto && b->hb.precision == DSEA_MIXED) any = true;
+        else fixed += (int64_t)b->hb.n_slices * b->hb.units_per_slice;
+    }
+    if (!any) return;
+    const int ci = pick_filling_shape([&](int c) {
+        int64_t u = fixed;
+        for (int k = 0; k < n; ++k) {
+            const dsea_box *b = boxes[k];
+            if (b->tile_auto && b->hb.precision == DSEA_MIXED)
+                u += units_with_tile(b->hb, b->mean_cap, kFillShapes[c][0], kFillShapes[c][1]);
+        }
+        return u;
+    });
+    for (int k = 0; k < n; ++k) {
+        dsea_box *b = boxes[k];
+        if (!(b->tile_auto && b->hb.precision == DSEA_MIXED)) continue;
+        if (fit_tile(b->hb, b->mean_cap, kFillShapes[ci][0], kFillShapes[ci][1])) {
+            b->params.tile_y = b->hb.tile_y;
+            b->params.tile_z = b->hb.tile_z;
+        }
+    }
+}
 
 void multi_free(MultiPlan &mp)
 {

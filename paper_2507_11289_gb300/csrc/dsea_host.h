@@ -35,6 +35,7 @@ struct dsea_box {
     bool registered = false;
     dsea_params params{};
     double mean_cap = 0;              // expected atoms per cell used for stage sizing
+    bool tile_auto = false;           // unit shape not requested: launches may re-choose it
     dsea::BoxDev hb{};
     dsea::BoxDev *db = nullptr;
     std::vector<std::pair<void *, size_t>> allocs;   // live device allocations and their sizes
@@ -83,6 +84,12 @@ int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t stream);
 // After the launch has been enqueued: advance the host step counters.
 void multi_commit(dsea_box *const *boxes, const int64_t *steps, int n);
 void multi_free(MultiPlan &mp);
+
+// Give every mixed-precision box of a launch whose unit shape is automatic
+// (tile_auto) the launch-filling shape of the whole set: the largest candidate
+// whose units per step, over all boxes, reach twice the resident warp stages.
+// Host arithmetic only; a shape never changes a result.
+void retile_for_launch(dsea_box *const *boxes, int n);
 
 // Geometry, cell capacity and work-unit shape of a box (no allocation).
 int box_geometry(int n_slices, const double *L, int64_t n_atoms, dsea_params &p, BoxDev &hb);

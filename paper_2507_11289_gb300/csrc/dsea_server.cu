@@ -156,6 +156,10 @@ void run(dsea_server *s)
                 steps[k] = std::min<int64_t>(running[k]->remaining, s->segment);
                 work += (double)running[k]->desc.n_atoms * (double)steps[k];
             }
+            // the jobs present choose the unit shape of this launch (when the
+            // server's params leave it automatic): small units while few jobs
+            // run, larger ones once they fill the GPU together
+            dsea::retile_for_launch(boxes.data(), n);
             rc = dsea::multi_prepare(s->mp, boxes.data(), steps.data(), n);
             if (!rc) {
                 cudaEventRecord(s->ev0, s->stream);

@@ -101,6 +101,7 @@ _SIGS = {
     "dsea_batch_advance": (_I, [_P, ctypes.POINTER(_I64)]),
     "dsea_batch_destroy": (_I, [_P]),
     "dsea_autotune": (_I, [_P, _I, ctypes.POINTER(Params)]),
+    "dsea_batch_autotune": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dsea_server_create": (_I, [ctypes.c_size_t, ctypes.POINTER(Params), _I, _P, ctypes.POINTER(_P)]),
     "dsea_server_submit": (_I, [_P, ctypes.POINTER(BoxDesc), _I64, ctypes.POINTER(ctypes.c_uint64)]),
     "dsea_server_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
@@ -344,6 +345,15 @@ def batch_create(handles):
 def batch_advance(batch, steps):
     s = (ctypes.c_int64 * len(steps))(*[int(x) for x in steps])
     _check(load().dsea_batch_advance(batch, s), "dsea_batch_advance")
+
+
+def batch_autotune(batch, trial_steps: int = 3) -> tuple[int, int]:
+    """One unit shape for every box of the batch, timed on the batch itself;
+    returns (tile_y, tile_z)."""
+    ty, tz = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().dsea_batch_autotune(batch, int(trial_steps), ctypes.byref(ty), ctypes.byref(tz)),
+           "dsea_batch_autotune")
+    return ty.value, tz.value
 
 
 def batch_destroy(batch):

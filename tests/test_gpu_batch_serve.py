@@ -43,6 +43,34 @@ def test_batch_equals_alone_bitwise():
             b.close()
 
 
+def test_batch_autotune_keeps_results_and_state():
+    """The batch autotuner times its candidates on the batch from snapshots:
+    the boxes' steps and states are unchanged by it, every box ends on the
+    chosen shape (or the largest that fits it), and the run continues to the
+    same bits as each box advanced alone."""
+    states = _boxes(5, seed=6)
+    ref = [_alone(s, 30) for s in states]
+    boxes = [dsea.Box(*s, precision=dsea.MIXED) for s in states]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        dsea.batch_advance(bt, [10] * 5)
+        ty, tz = dsea.batch_autotune(bt, trial_steps=2)
+        assert (ty, tz) in {(1, 2), (2, 2), (1, 4), (2, 4), (3, 3), (4, 4)}
+        for b in boxes:
+            info = b.info()
+            assert b.observables()["step"] == 10        # trials left the state untouched
+            assert 1 <= info["tile_y"] <= ty and 1 <= info["tile_z"] <= tz
+        dsea.batch_advance(bt, [20] * 5)
+        dsea.batch_destroy(bt)
+        for b, (r, v, o) in zip(boxes, ref):
+            assert np.array_equal(b.positions(), r)
+            assert np.array_equal(b.velocities(), v)
+            assert b.observables() == o
+    finally:
+        for b in boxes:
+            b.close()
+
+
 def test_batch_fp64_matches_oracle():
     states = _boxes(3, seed=9)
     boxes = [dsea.Box(*s, precision=dsea.FP64) for s in states]
@@ -130,33 +158,51 @@ def test_autotune_choice_does_not_leak_across_densities():
     dense one of about the same edge are different classes (mean atoms per
     cell; below rho 0.77 the cells are also larger), and so are a 17^3-cell
     box and the 43^3-cell 1M-atom box at the same density (total cells):
-    tuning the first of each pair leaves the second on the default shape.  Run
-    in a fresh process: the cache lives as long as the library."""
+    tuning the first of each pair leaves the second on its untuned shape.  The
+    untuned mixed shape is the launch-filling one: the largest of 4x4, 3x3,
+    2x4, 2x2, 1x4, 1x2 home cells whose units per step reach twice the
+    resident warp stages (32 per SM), else 1x2.  Run in a fresh process: the
+    cache lives as long as the library."""
+    import json
+    import os
     import subprocess
     import sys
     code = """
 import json
+import torch
 from paper_2507_11289_gb300 import dsea, inputs
-out = {}
-for name, n_i, rho in (("dilute", 22, 0.55), ("dense", 25, 0.8), ("big", 64, 0.8)):
+cases = (("dilute", 22, 0.55), ("dense", 25, 0.8), ("big", 64, 0.8))
+def make(n_i, rho):
     pos, box = inputs.fcc_lattice(n_i, rho)
-    vel = inputs.maxwell_boltzmann(len(pos), 1.0, 3)
-    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+    return dsea.Box(pos, inputs.maxwell_boltzmann(len(pos), 1.0, 3), box, precision=dsea.MIXED)
+out = {"sms": torch.cuda.get_device_properties(0).multi_processor_count}
+for name, n_i, rho in cases:
+    with make(n_i, rho) as b:
         inf = b.info()
-        out[name] = {"cells": inf["cells"], "cap": inf["cell_capacity"],
-                     "tile": [inf["tile_y"], inf["tile_z"]]}
+        out[name] = {"cells": inf["cells"], "cap": inf["cell_capacity"], "slices": inf["n_slices"],
+                     "untuned": [inf["tile_y"], inf["tile_z"]]}
+for name, n_i, rho in cases:
+    with make(n_i, rho) as b:
+        inf = b.info()
+        out[name]["tile"] = [inf["tile_y"], inf["tile_z"]]
         if name != "big":
             p = b.autotune(trial_steps=2)
             out[name]["tuned"] = [p["tile_y"], p["tile_z"]]
 print(json.dumps(out))
 """
-    import json
-    import os
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     out = json.loads(r.stdout.strip().splitlines()[-1])
     d, e, g = out["dilute"], out["dense"], out["big"]
-    assert e["tile"] == [2, 4], out                                # the mixed default, untouched
+    want = 2 * out["sms"] * 32
+
+    def units(c, ty, tz):
+        return c["slices"] * -(-c["cells"][1] // ty) * -(-c["cells"][2] // tz)
+
+    for c in (d, e, g):   # the launch-filling rule, restated
+        fill = [s for s in ((4, 4), (3, 3), (2, 4), (2, 2), (1, 4), (1, 2)) if units(c, *s) >= want]
+        assert c["untuned"] == list(fill[0] if fill else (1, 2)), out
+    assert e["tile"] == e["untuned"], out                          # not the dilute box's choice
     assert g["cap"] == e["cap"] and min(g["cells"][1:]) >= 16 and min(e["cells"][1:]) >= 16
-    assert g["tile"] == [2, 4], out                                # not the 17^3 box's choice
+    assert g["tile"] == g["untuned"], out                          # not the 17^3 box's choice
