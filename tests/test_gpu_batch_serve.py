@@ -131,6 +131,42 @@ def test_server_results_same_alone_and_in_mix():
         dsea.server_destroy(srv)
 
 
+def test_server_reshapes_units_as_jobs_leave():
+    """Two 1,048,576-atom jobs fill the GPU together with 4 x 4-cell units
+    (2 x 5,203 units per step against twice the 4,864 resident warp stages);
+    once the shorter one has finished, the longer one runs alone at 2 x 4
+    (10,406 units).  The server re-chooses the shape at every launch, and a
+    shape never changes a result: each job equals its run alone bit for bit."""
+    import torch
+    pos, box = inputs.fcc_lattice(64, 0.8)
+    vels = [inputs.maxwell_boltzmann(len(pos), 1.5, seed) for seed in (21, 22)]
+    steps = [60, 20]
+    with dsea.Box(pos, vels[0], box, precision=dsea.MIXED) as b:
+        info = b.info()
+    cells = info["cells"]
+    stages = torch.cuda.get_device_properties(0).multi_processor_count * 32
+
+    def units(ty, tz):
+        return info["n_slices"] * -(-cells[1] // ty) * -(-cells[2] // tz)
+
+    def rule(n_jobs):
+        fill = [s for s in ((4, 4), (3, 3), (2, 4), (2, 2), (1, 4), (1, 2)) if n_jobs * units(*s) >= 2 * stages]
+        return fill[0] if fill else (1, 2)
+
+    assert rule(2) != rule(1)                # the test exercises a change of shape
+    srv = dsea.server_create(16 << 30, dsea.make_params(precision=dsea.MIXED), 10, 0)
+    try:
+        ids = [dsea.server_submit(srv, pos, v, box, k) for v, k in zip(vels, steps)]
+        dsea.server_drain(srv)
+        res = [dsea.server_result(srv, jid, len(pos)) for jid in ids]
+    finally:
+        dsea.server_destroy(srv)
+    for (r, v, o, _, _), vel, k in zip(res, vels, steps):
+        ra, va, oa = _alone((pos, vel, box), k)
+        assert np.array_equal(r, ra) and np.array_equal(v, va)
+        assert o == oa and o["step"] == k
+
+
 def test_server_rejects_job_over_budget():
     pos, vel, box = inputs.SMALL_4K.state()
     srv = dsea.server_create(1 << 20, None, 10, 0)          # 1 MiB budget
