@@ -1557,6 +1557,97 @@ __global__ void __launch_bounds__(kThreads) k_bin(const BoxDev *bp, const double
     }
 }
 
+// After binning: one warp per cell moves the cell's arrivals (every atom
+// k_bin placed, in the order its atomics gave) to the front slots in atom-id
+// order, after any stayers, and makes them stayers.  That is the cell's
+// canonical order already (stayers in slot order, then arrivals by id), so
+// no result changes; but the first step's readers then find stayers and
+// skip ranking a whole cell of arrivals, a quadratic loop of dependent loads
+// that made the first step ten times slower than the rest.  All of a cell's
+// records are read into registers before any is written: the two slot ranges
+// may overlap.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_settle(const BoxDev *bp)
+{
+    const BoxDev &B = *bp;
+    const int lane = threadIdx.x & 31;
+    const int p = (int)(B.step & 1);
+    const unsigned tag = (unsigned)(B.step + 1);
+    const long long S = B.n_slots;
+    const long long warps = (long long)gridDim.x * (kThreads / 32);
+    for (long long gc = (long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); gc < B.n_cells;
+         gc += warps) {
+        const unsigned long long ws = B.cnt[p][gc], wa = B.arr[p][gc];
+        const int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;
+        const int n_a = ((unsigned)(wa >> 32) == tag) ? (int)(unsigned)wa : 0;
+        if (n_a == 0 || n_s + n_a > B.cap || n_a > 128) continue;   // nothing to do, or overflowed
+        const long long abase = gc * B.cap + B.cap - n_a;            // the first arrival's slot
+        int idm[4];
+        double rx[4], ry[4], rz[4], vx[4], vy[4], vz[4];
+        float4 qm[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int a = lane + 32 * m;
+            idm[m] = 0x7fffffff;
+            if (a < n_a) {
+                const long long slot = abase + a;
+                rx[m] = B.r[p][slot];
+                ry[m] = B.r[p][S + slot];
+                rz[m] = B.r[p][2 * S + slot];
+                if (PREC == 1) {
+                    vx[m] = B.vf[p][slot];
+                    vy[m] = B.vf[p][S + slot];
+                    vz[m] = B.vf[p][2 * S + slot];
+                    qm[m] = B.q[p][slot];
+                    idm[m] = __float_as_int(qm[m].w);
+                } else {
+                    vx[m] = B.v[p][slot];
+                    vy[m] = B.v[p][S + slot];
+                    vz[m] = B.v[p][2 * S + slot];
+                    idm[m] = B.id[p][slot];
+                }
+            }
+        }
+        // rank by id among the cell's arrivals (ids are distinct)
+        int rk[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int mb = 0; mb < 4; ++mb) {   // n_a is the same on every lane
+            const int lim = min(32, n_a - 32 * mb);
+            for (int t = 0; t < lim; ++t) {
+                const int o = __shfl_sync(kFull, idm[mb], t);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) rk[m] += (o < idm[m]) ? 1 : 0;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int a = lane + 32 * m;
+            if (a < n_a) {
+                const long long slot = gc * B.cap + n_s + rk[m];
+                B.r[p][slot] = rx[m];
+                B.r[p][S + slot] = ry[m];
+                B.r[p][2 * S + slot] = rz[m];
+                if (PREC == 1) {
+                    B.vf[p][slot] = (float)vx[m];
+                    B.vf[p][S + slot] = (float)vy[m];
+                    B.vf[p][2 * S + slot] = (float)vz[m];
+                    B.q[p][slot] = qm[m];
+                } else {
+                    B.v[p][slot] = vx[m];
+                    B.v[p][S + slot] = vy[m];
+                    B.v[p][2 * S + slot] = vz[m];
+                    B.id[p][slot] = idm[m];
+                }
+            }
+        }
+        if (lane == 0) {
+            B.cnt[p][gc] = ((unsigned long long)tag << 32) | (unsigned long long)(n_s + n_a);
+            B.arr[p][gc] = (unsigned long long)tag << 32;
+        }
+    }
+}
+
 // FP64 form, one step or force pass: one CTA per unit.
 template <bool INTEGRATE, bool OBS>
 __global__ void __launch_bounds__(kThreads) k_units_f64(const BoxDev *bp, long long s_abs, int first)
@@ -1887,6 +1978,12 @@ cudaError_t launch_bin(const BoxDev &hb, const BoxDev *db, const double *pos, co
     const int grid = (int)(blocks < 65535 ? blocks : 65535);
     if (hb.precision == 1) k_bin<1><<<grid, kThreads, 0, stream>>>(db, pos, vel);
     else k_bin<0><<<grid, kThreads, 0, stream>>>(db, pos, vel);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long sblocks = (hb.n_cells + kThreads / 32 - 1) / (kThreads / 32);
+    const int sgrid = (int)(sblocks < 65535 ? sblocks : 65535);
+    if (hb.precision == 1) k_settle<1><<<sgrid, kThreads, 0, stream>>>(db);
+    else k_settle<0><<<sgrid, kThreads, 0, stream>>>(db);
     return cudaGetLastError();
 }
 
