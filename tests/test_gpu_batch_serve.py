@@ -167,6 +167,35 @@ def test_server_reshapes_units_as_jobs_leave():
         assert o == oa and o["step"] == k
 
 
+def test_server_isolates_a_failing_job():
+    """A job whose atom jumps past a whole slice in its first step fails with
+    the migration status; the jobs that shared its launch finish with the
+    results they have alone, and the server keeps admitting work.  One-step
+    segments end the failing job after the step that reports it."""
+    states = _boxes(3, seed=8)
+    pos, vel, box = inputs.SMALL_4K.state()
+    vel = vel.copy()
+    vel[0] = [2000.0, 0.0, 0.0]        # 10 sigma in one step: more than one 4.3-sigma slice
+    steps = [12, 9, 7]
+    srv = dsea.server_create(8 << 30, dsea.make_params(precision=dsea.MIXED), 1, 0)
+    try:
+        good = [dsea.server_submit(srv, *states[0], steps[0])]
+        bad = dsea.server_submit(srv, pos, vel, box, 5, n_slices=4)
+        good += [dsea.server_submit(srv, *states[k], steps[k]) for k in (1, 2)]
+        dsea.server_drain(srv)
+        assert dsea.server_poll(srv, bad) == dsea.ERR_MIGRATION
+        for jid, st, k in zip(good, states, steps):
+            assert dsea.server_poll(srv, jid) == 2
+            r, v, o, _, _ = dsea.server_result(srv, jid, len(st[0]))
+            ra, va, oa = _alone(st, k)
+            assert np.array_equal(r, ra) and np.array_equal(v, va) and o == oa
+        later = dsea.server_submit(srv, *states[1], 4)
+        dsea.server_drain(srv)
+        assert dsea.server_poll(srv, later) == 2
+    finally:
+        dsea.server_destroy(srv)
+
+
 def test_server_rejects_job_over_budget():
     pos, vel, box = inputs.SMALL_4K.state()
     srv = dsea.server_create(1 << 20, None, 10, 0)          # 1 MiB budget
