@@ -84,3 +84,48 @@ def test_cell_box_pruning_beats_cluster_pairs_of_four_and_eight():
     assert e == pytest.approx(4 * np.pi / 3 * RC ** 3 * 0.8, rel=0.05)
     assert c4 > cb and c8 > c4
     assert c2 < cb
+
+
+def test_home_clusters_against_neighbour_atoms_cost_list_room():
+    """The finer scheme, each cluster of k home atoms pruning the neighbour
+    atoms against its own box, does cut the candidates below the cell box
+    (about 133 per atom for k = 4, 177 for k = 8, against 228), but each home
+    cell then keeps one list per cluster: about 480 entries for k = 4, more
+    than the 400-entry list window of a warp, and every raw neighbour entry is
+    tested against each of the cell's clusters instead of once."""
+    pos, L, nc, lc, cells = _setup()
+    rng = np.random.default_rng(0)
+    sample = rng.choice(sorted(cells), 150, replace=False)
+
+    def rel(ids, ref):
+        d = pos[ids] - ref
+        return d - L * np.round(d / L)
+
+    cand = {16: [], 8: [], 4: []}
+    kept = {16: [], 8: [], 4: []}
+    n_clusters = {16: [], 8: [], 4: []}
+    for c in sample:
+        home = np.array(cells[c])
+        ref = pos[home[0]]
+        n = rel(np.concatenate([np.array(cells[k]) for k in _neighbours(c, nc)]), ref)
+        h = rel(home, ref)
+        for k in cand:
+            tot = st = 0
+            hcl = _clusters(h, k, lc)
+            for lo, hi, m in hcl:
+                dd = np.maximum(np.maximum(lo - n, n - hi), 0.0)
+                keep = int(((dd * dd).sum(1) <= RC * RC).sum())
+                tot += m * keep
+                st += keep
+            cand[k].append(tot / len(home))
+            kept[k].append(st)
+            n_clusters[k].append(len(hcl))
+    c16, c8, c4 = (np.mean(cand[k]) for k in (16, 8, 4))
+    s16, s8, s4 = (np.mean(kept[k]) for k in (16, 8, 4))
+    print(f"home clusters x neighbour atoms, candidates per atom k=16/8/4: {c16:.0f} / {c8:.0f} / {c4:.0f}; "
+          f"list entries per home cell {s16:.0f} / {s8:.0f} / {s4:.0f}; "
+          f"box tests per raw entry {np.mean(n_clusters[16]):.1f} / {np.mean(n_clusters[8]):.1f} / "
+          f"{np.mean(n_clusters[4]):.1f}")
+    assert c4 < c8 < c16 and c4 < 0.65 * c16          # fewer candidates...
+    assert s4 > 400 and s4 > 1.8 * s16                 # ...for lists beyond a warp's window
+    assert np.mean(n_clusters[4]) > 3                  # and a box test per cluster per entry
