@@ -223,12 +223,13 @@ int dsea_batch_destroy(dsea_batch *batch);
 /* ---- autotuning -------------------------------------------------------- */
 
 /* Time each candidate work-unit shape (tile_y x tile_z home cells) for
- * trial_steps steps on a scratch copy of the box and keep the fastest; the
+ * trial_steps steps from a snapshot of the box's state (taken through the
+ * box's allocator, restored after each trial) and keep the fastest; the
  * choice is cached per size class (cells along y and z up to 16, cell layers
  * per slice, cell capacity, precision), applied to the box and used as the
- * default shape of later boxes of the same class.  The tile shape never changes a result: each atom's force is
- * summed in the same order whatever the shape.  *chosen (may be NULL)
- * receives the parameters in effect. */
+ * default shape of later boxes of the same class.  The tile shape never
+ * changes a result: each atom's force is summed in the same order whatever
+ * the shape.  *chosen (may be NULL) receives the parameters in effect. */
 int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);
 
 /* Choose one unit shape for every box of a batch: each candidate (the same
@@ -239,10 +240,12 @@ int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);
  * fastest shape; *tile_y, *tile_z (may be NULL) receive it.  Many boxes in
  * one launch fill the GPU by themselves, so the batch's best shape is
  * usually larger than what dsea_autotune picks for a small box alone.  The
- * boxes leave the automatic shape; the lone-box cache is not changed.  Snapshots take device memory of the size of every
- * box's state; DSEA_ERR_OOM if it is not there (the boxes are unchanged).
- * The shape never changes a result.  Results: DSEA_OK, DSEA_ERR_INVALID_ARG
- * (NULL batch, trial_steps <= 0), or a latched device error of a box. */
+ * boxes leave the automatic shape; the lone-box cache is not changed.  The
+ * snapshots, as large as every box's state, come from each box's allocator
+ * and are released before the call returns; DSEA_ERR_OOM if they do not fit
+ * (the boxes are unchanged).  The shape never changes a result.  Results:
+ * DSEA_OK, DSEA_ERR_INVALID_ARG (NULL batch, trial_steps <= 0), or a latched
+ * device error of a box. */
 int dsea_batch_autotune(dsea_batch *batch, int trial_steps, int *tile_y, int *tile_z);
 
 /* ---- serving ----------------------------------------------------------- */

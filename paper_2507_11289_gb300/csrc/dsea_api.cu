@@ -345,12 +345,13 @@ struct BoxSnapshot {
         b_r = sizeof(double) * 3 * hb.n_slots;
         b_q = sizeof(float4) * hb.n_slots;
         b_v = (mixed ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots;
-        const bool ok = cudaMalloc(&s_cnt, b_cnt) == cudaSuccess &&
-                        (mixed || cudaMalloc(&s_id, b_id) == cudaSuccess) &&
-                        cudaMalloc(&s_r, b_r) == cudaSuccess && cudaMalloc(&s_v, b_v) == cudaSuccess &&
-                        (!mixed || cudaMalloc(&s_q, b_q) == cudaSuccess);
-        if (!ok) {
-            cudaGetLastError();
+        // through the box's own allocator (the caller's pool, when it gave one)
+        s_cnt = dev_alloc(b, b_cnt);
+        if (!mixed) s_id = dev_alloc(b, b_id);
+        s_r = dev_alloc(b, b_r);
+        s_v = dev_alloc(b, b_v);
+        if (mixed) s_q = dev_alloc(b, b_q);
+        if (!s_cnt || (!mixed && !s_id) || !s_r || !s_v || (mixed && !s_q)) {
             release();
             return DSEA_ERR_OOM;
         }
@@ -367,7 +368,7 @@ struct BoxSnapshot {
     void release()
     {
         for (void *q : {s_cnt, s_id, s_r, s_v, s_q})
-            if (q) cudaFree(q);
+            if (q) dev_free(b, q);
         s_cnt = s_id = s_r = s_v = s_q = nullptr;
     }
     ~BoxSnapshot() { release(); }

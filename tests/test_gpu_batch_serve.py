@@ -54,7 +54,16 @@ def test_batch_autotune_keeps_results_and_state():
     try:
         bt = dsea.batch_create([b.h for b in boxes])
         dsea.batch_advance(bt, [10] * 5)
+        import torch
+        torch.cuda.synchronize()
+        m0 = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        n_slots = sum(b.info()["cells"][0] * b.info()["cells"][1] * b.info()["cells"][2] * b.info()["cell_capacity"]
+                      for b in boxes)
         ty, tz = dsea.batch_autotune(bt, trial_steps=2)
+        # the snapshots (at least r and q of every slot) came from the boxes' allocator, torch's here
+        assert torch.cuda.max_memory_allocated() - m0 >= n_slots * (24 + 16)
+        assert torch.cuda.memory_allocated() == m0
         assert (ty, tz) in {(1, 2), (2, 2), (1, 4), (2, 4), (3, 3), (4, 4)}
         for b in boxes:
             info = b.info()
