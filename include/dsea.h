@@ -307,8 +307,10 @@ int dsea_server_destroy(dsea_server *srv);
  *             a status word back to the host.
  * Returns DSEA_ERR_SCRATCH_LIMIT, before touching the GPU, when the box needs
  * more than the 64 MiB (at density 0.8: about 290,000 atoms in FP64, 240,000
- * in the mixed form).  The first call on a device looks up the array's device
- * address; make that first call before any stream capture.  Every call shares
+ * in the mixed form).  Because every call waits for its stream and reads the
+ * status word back, no call may be made while a stream is being captured
+ * into a CUDA graph (the first call on a device also looks up the array's
+ * device address, which capture does not allow either).  Every call shares
  * the array: calls that overlap on the GPU, from other streams or host
  * threads, race and must be serialised by the caller. */
 #define DSEA_ERR_SCRATCH_LIMIT -11 /* problem larger than the fixed scratch */
