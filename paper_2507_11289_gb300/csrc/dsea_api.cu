@@ -205,13 +205,29 @@ int ring_launch_single(dsea_box *b, int64_t n)
     BoxDev &hb = b->hb;
     const int64_t U = (int64_t)hb.n_slices * hb.units_per_slice;
     if (n + 1 > b->step_base_cap) {
-        b->step_base_cap = std::max<int64_t>(n + 1, 1024);
-        b->d_step_base = (int64_t *)dev_alloc(b, sizeof(int64_t) * b->step_base_cap);
-        b->d_active = (int *)dev_alloc(b, sizeof(int) * b->step_base_cap);
-        if (!b->d_step_base || !b->d_active) return DSEA_ERR_OOM;
-        std::vector<int> ones(b->step_base_cap, 1);
-        CU(cudaMemcpyAsync(b->d_active, ones.data(), sizeof(int) * ones.size(),
-                           cudaMemcpyHostToDevice, b->stream));
+        // grow the plan arrays; the box keeps its old ones if an allocation fails
+        const int64_t cap = std::max<int64_t>(n + 1, 1024);
+        int64_t *sb = (int64_t *)dev_alloc(b, sizeof(int64_t) * cap);
+        int *act = (int *)dev_alloc(b, sizeof(int) * cap);
+        if (!sb || !act) {
+            if (sb) dev_free(b, sb);
+            if (act) dev_free(b, act);
+            return DSEA_ERR_OOM;
+        }
+        std::vector<int> ones(cap, 1);
+        const cudaError_t e = cudaMemcpyAsync(act, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice,
+                                              b->stream);
+        if (e == cudaSuccess) cudaStreamSynchronize(b->stream);   // `ones` is pageable and local
+        if (e != cudaSuccess) {
+            dev_free(b, sb);
+            dev_free(b, act);
+            return map_cuda(e);
+        }
+        if (b->d_step_base) dev_free(b, b->d_step_base);
+        if (b->d_active) dev_free(b, b->d_active);
+        b->d_step_base = sb;
+        b->d_active = act;
+        b->step_base_cap = cap;
     }
     std::vector<int64_t> sb(n + 1);
     for (int64_t s = 0; s <= n; ++s) sb[s] = s * U;
@@ -272,12 +288,18 @@ int ensure_outputs(dsea_box *b)
 {
     if (b->outputs_valid) return check_device_error(b);
     BoxDev &hb = b->hb;
-    if (!hb.out_r) {
+    if (!hb.out_r) {   // all three or none
         const size_t bytes = sizeof(double) * 3 * (size_t)std::max<int64_t>(hb.n_atoms, 1);
-        hb.out_r = (double *)dev_alloc(b, bytes);
-        hb.out_v = (double *)dev_alloc(b, bytes);
-        hb.out_f = (double *)dev_alloc(b, bytes);
-        if (!hb.out_r || !hb.out_v || !hb.out_f) return DSEA_ERR_OOM;
+        double *o[3];
+        for (auto &q : o) q = (double *)dev_alloc(b, bytes);
+        if (!o[0] || !o[1] || !o[2]) {
+            for (double *q : o)
+                if (q) dev_free(b, q);
+            return DSEA_ERR_OOM;
+        }
+        hb.out_r = o[0];
+        hb.out_v = o[1];
+        hb.out_f = o[2];
     }
     int rc = upload_desc(b);
     if (rc) return rc;
@@ -506,6 +528,84 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
 
 }  // namespace
 
+namespace {
+
+// Registration proper; dsea_register_kernel undoes it when it fails.
+int register_impl(dsea_box *b, const dsea_params *params)
+{
+    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0, 0.0};
+    if (params) p = *params;
+    if (!(p.temperature >= 0.0) || !std::isfinite(p.temperature)) return DSEA_ERR_INVALID_ARG;
+    CU(cudaSetDevice(b->device));
+    BoxDev &hb = b->hb;
+    const bool tile_auto = p.tile_y == 0 && p.tile_z == 0;
+    int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
+    if (rc0) return rc0;
+    b->tile_auto = tile_auto;
+    hb.walls_x = b->walls_x;
+    const int n_s = hb.n_slices;
+    b->params = p;
+
+    // device state
+    b->db = (BoxDev *)dev_alloc(b, sizeof(BoxDev));
+    hb.err = (int *)dev_alloc(b, sizeof(int));
+    hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * n_s);
+    const int64_t max_units = hb.n_cells;   // any tile shape has at most one unit per cell
+    hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * dsea::kObsStride * (size_t)max_units);
+    hb.T0 = p.temperature;
+    for (int q = 0; q < 2; ++q) {
+        hb.th_part[q] = nullptr;
+        hb.th_lam[q] = nullptr;
+        if (hb.T0 > 0.0) {
+            hb.th_part[q] = (double *)dev_alloc(b, sizeof(double) * 2 * (size_t)max_units);
+            hb.th_lam[q] = (double *)dev_alloc(b, sizeof(double) * n_s);
+            if (!hb.th_part[q] || !hb.th_lam[q]) return DSEA_ERR_OOM;
+        }
+    }
+    b->d_obs3 = (double *)dev_alloc(b, sizeof(double) * 3);
+    b->d_cum = (int64_t *)dev_alloc(b, sizeof(int64_t) * 2);
+    b->d_ticket = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long));
+    b->d_launch_err = (int *)dev_alloc(b, sizeof(int));
+    if (!b->db || !hb.err || !hb.done || !hb.unit_obs || !b->d_obs3 || !b->d_cum || !b->d_ticket ||
+        !b->d_launch_err)
+        return DSEA_ERR_OOM;
+    for (int q = 0; q < 2; ++q) {
+        // stayer and arrival counts of every cell, one allocation
+        hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * 2 * hb.n_cells);
+        hb.arr[q] = hb.cnt[q] ? hb.cnt[q] + hb.n_cells : nullptr;
+        hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        hb.id[q] = nullptr;
+        hb.v[q] = nullptr;
+        hb.vf[q] = nullptr;
+        hb.q[q] = nullptr;
+        if (p.precision == DSEA_MIXED) {   // the atom id travels in q.w
+            hb.vf[q] = (float *)dev_alloc(b, sizeof(float) * 3 * hb.n_slots);
+            hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
+        } else {
+            hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
+            hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
+        }
+        if (!hb.cnt[q] || !hb.r[q] ||
+            (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : (!hb.v[q] || !hb.id[q])))
+            return DSEA_ERR_OOM;
+        CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * 2 * hb.n_cells, b->stream));
+    }
+    CU(cudaMemsetAsync(hb.err, 0, sizeof(int), b->stream));
+    // bin the initial atoms (copied to the device by dsea_box_create) into the
+    // buffer of step 0, then release those copies
+    int rc = upload_desc(b);
+    if (!rc) rc = map_cuda(dsea::launch_bin(hb, b->db, b->d_pos0, b->d_vel0, b->stream));
+    if (!rc) rc = check_device_error(b);
+    if (rc) return rc;
+    if (b->d_pos0) dev_free(b, b->d_pos0);
+    if (b->d_vel0) dev_free(b, b->d_vel0);
+    b->d_pos0 = b->d_vel0 = nullptr;
+    b->registered = true;
+    return DSEA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *dsea_version(void) { return "0.1.0"; }
@@ -579,76 +679,31 @@ int dsea_register_kernel(dsea_box *b, int kind, int o_in, int o_out, const dsea_
     if (!b) return DSEA_ERR_INVALID_ARG;
     if (b->registered) return DSEA_ERR_STATE;
     if (kind != DSEA_KERNEL_LJ_TS || o_in != 1 || o_out != 1) return DSEA_ERR_INVALID_ARG;
-    dsea_params p{2.5, 0.005, DSEA_FP64, DSEA_SCHED_RING, 0, 0, 0, 0, 0.0};
-    if (params) p = *params;
-    if (!(p.temperature >= 0.0) || !std::isfinite(p.temperature)) return DSEA_ERR_INVALID_ARG;
-    CU(cudaSetDevice(b->device));
-    BoxDev &hb = b->hb;
-    const bool tile_auto = p.tile_y == 0 && p.tile_z == 0;
-    int rc0 = setup_geometry(b->n_slices_req, b->L, hb.n_atoms, p, hb, b->mean_cap);
-    if (rc0) return rc0;
-    b->tile_auto = tile_auto;
-    hb.walls_x = b->walls_x;
-    const int n_s = hb.n_slices;
-    b->params = p;
-
-    // device state
-    b->db = (BoxDev *)dev_alloc(b, sizeof(BoxDev));
-    hb.err = (int *)dev_alloc(b, sizeof(int));
-    hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * n_s);
-    const int64_t max_units = hb.n_cells;   // any tile shape has at most one unit per cell
-    hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * dsea::kObsStride * (size_t)max_units);
-    hb.T0 = p.temperature;
-    for (int q = 0; q < 2; ++q) {
-        hb.th_part[q] = nullptr;
-        hb.th_lam[q] = nullptr;
-        if (hb.T0 > 0.0) {
-            hb.th_part[q] = (double *)dev_alloc(b, sizeof(double) * 2 * (size_t)max_units);
-            hb.th_lam[q] = (double *)dev_alloc(b, sizeof(double) * n_s);
-            if (!hb.th_part[q] || !hb.th_lam[q]) return DSEA_ERR_OOM;
+    // a failed registration leaves the box as dsea_box_create made it: what it
+    // allocated is released and the descriptor restored, so it may be retried
+    const size_t n_allocs0 = b->allocs.size();
+    const BoxDev hb0 = b->hb;
+    const dsea_params p0 = b->params;
+    const double mean_cap0 = b->mean_cap;
+    const int rc = register_impl(b, params);
+    if (rc) {
+        cudaStreamSynchronize(b->stream);
+        cudaGetLastError();
+        while (b->allocs.size() > n_allocs0) {
+            const auto a = b->allocs.back();
+            b->allocs.pop_back();
+            dev_release(b, a.first);
+            b->device_bytes -= a.second;
         }
+        b->hb = hb0;
+        b->params = p0;
+        b->mean_cap = mean_cap0;
+        b->tile_auto = false;
+        b->latched = DSEA_OK;
     }
-    b->d_obs3 = (double *)dev_alloc(b, sizeof(double) * 3);
-    b->d_cum = (int64_t *)dev_alloc(b, sizeof(int64_t) * 2);
-    b->d_ticket = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long));
-    b->d_launch_err = (int *)dev_alloc(b, sizeof(int));
-    if (!b->db || !hb.err || !hb.done || !hb.unit_obs || !b->d_obs3 || !b->d_cum || !b->d_ticket ||
-        !b->d_launch_err)
-        return DSEA_ERR_OOM;
-    for (int q = 0; q < 2; ++q) {
-        // stayer and arrival counts of every cell, one allocation
-        hb.cnt[q] = (unsigned long long *)dev_alloc(b, sizeof(unsigned long long) * 2 * hb.n_cells);
-        hb.arr[q] = hb.cnt[q] ? hb.cnt[q] + hb.n_cells : nullptr;
-        hb.r[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
-        hb.id[q] = nullptr;
-        hb.v[q] = nullptr;
-        hb.vf[q] = nullptr;
-        hb.q[q] = nullptr;
-        if (p.precision == DSEA_MIXED) {   // the atom id travels in q.w
-            hb.vf[q] = (float *)dev_alloc(b, sizeof(float) * 3 * hb.n_slots);
-            hb.q[q] = (float4 *)dev_alloc(b, sizeof(float4) * hb.n_slots);
-        } else {
-            hb.id[q] = (int *)dev_alloc(b, sizeof(int) * hb.n_slots);
-            hb.v[q] = (double *)dev_alloc(b, sizeof(double) * 3 * hb.n_slots);
-        }
-        if (!hb.cnt[q] || !hb.r[q] ||
-            (p.precision == DSEA_MIXED ? (!hb.vf[q] || !hb.q[q]) : (!hb.v[q] || !hb.id[q])))
-            return DSEA_ERR_OOM;
-        CU(cudaMemsetAsync(hb.cnt[q], 0, sizeof(unsigned long long) * 2 * hb.n_cells, b->stream));
-    }
-    CU(cudaMemsetAsync(hb.err, 0, sizeof(int), b->stream));
-    // bin the initial atoms (copied to the device by dsea_box_create) into the
-    // buffer of step 0, then release those copies
-    int rc = upload_desc(b);
-    if (!rc) rc = map_cuda(dsea::launch_bin(hb, b->db, b->d_pos0, b->d_vel0, b->stream));
-    if (!rc) rc = check_device_error(b);
-    if (rc) return rc;
-    if (b->d_pos0) dev_free(b, b->d_pos0);
-    if (b->d_vel0) dev_free(b, b->d_vel0);
-    b->d_pos0 = b->d_vel0 = nullptr;
-    b->registered = true;
-    return DSEA_OK;
+    return rc;
 }
+
 
 int dsea_advance(dsea_box *b, int64_t n_steps)
 {
@@ -768,7 +823,7 @@ int dsea_box_destroy(dsea_box *b)
 {
     NvtxRange nvtx_range("dsea_box_destroy");
     if (!b) return DSEA_ERR_INVALID_ARG;
-    if (b->registered) cudaStreamSynchronize(b->stream);
+    cudaStreamSynchronize(b->stream);   // nothing of the box's may still run
     dev_free_all(b);
     delete b;
     return DSEA_OK;
