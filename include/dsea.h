@@ -45,6 +45,8 @@ extern "C" {
 #define DSEA_ERR_STATE -8       /* call out of order (e.g. no kernel registered) */
 #define DSEA_ERR_NOT_FOUND -9   /* unknown job id */
 #define DSEA_ERR_NO_DEVICE -10  /* no CUDA device available */
+#define DSEA_ERR_BOUNDS -12     /* checked build only: a kernel met an index out of range
+                                   (it skipped the access; the box's state is not valid) */
 
 /* ---- enums ------------------------------------------------------------- */
 #define DSEA_FP64 0  /* all pair arithmetic in FP64 */

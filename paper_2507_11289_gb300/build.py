@@ -3,6 +3,13 @@
 Each translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into paper_2507_11289_gb300/_build/libdsea.so (CUDA runtime linked
 statically).  Nothing is installed outside the source tree.
+
+build(checked=True) makes the checked variant, _build/libdsea_checked.so,
+with -DDSEA_CHECKED=1: every computed global index and shared-memory list
+position is tested before use, and one out of range fails the box with
+DSEA_ERR_BOUNDS instead of touching memory (a bounds checker for a pool
+where compute-sanitizer is not available).  It runs the same arithmetic in
+the same order, so its results equal the release build's bit for bit.
 """
 from __future__ import annotations
 
@@ -17,6 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdsea.so")
+LIB_CHECKED = os.path.join(BUILD, "libdsea_checked.so")
 SOURCES = ["dsea_kernels.cu", "dsea_api.cu", "dsea_server.cu", "dsea_noalloc.cu", "dsea_dataset.cu",
            "dsea_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,24 +44,28 @@ def _inputs():
     return files
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if needed) and return the path of libdsea.so."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile (if needed) and return the path of libdsea.so (checked:
+    libdsea_checked.so, the bounds-checked variant)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
+    variant = ["-DDSEA_CHECKED=1"] if checked else []
     common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-pthread",
-              "-I", INCLUDE, "-I", CSRC, *extra_flags]
+              "-I", INCLUDE, "-I", CSRC, *variant, *extra_flags]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [*common, "-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -64,15 +76,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-pthread", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError(f"link of libdsea.so failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{res.stderr}")
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -41,6 +41,7 @@ int map_device_error(int code)
     case dsea::kErrCapacity: return DSEA_ERR_CAPACITY;
     case dsea::kErrMigration: return DSEA_ERR_MIGRATION;
     case dsea::kErrTimeout: return DSEA_ERR_TIMEOUT;
+    case dsea::kErrBounds: return DSEA_ERR_BOUNDS;
     default: return DSEA_ERR_CUDA;
     }
 }
@@ -625,6 +626,7 @@ const char *dsea_status_string(int s)
     case DSEA_ERR_NOT_FOUND: return "unknown job";
     case DSEA_ERR_NO_DEVICE: return "no CUDA device";
     case DSEA_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed no-allocation scratch";
+    case DSEA_ERR_BOUNDS: return "index out of range (checked build)";
     default: return "unknown status";
     }
 }

@@ -7,6 +7,15 @@
 #include <cstddef>
 #include <cstdint>
 
+// DSEA_CHECKED=1 builds the checked variant of the library: every computed
+// global index (slots, cells, atom ids, units, slices) and shared-memory list
+// position is tested before it is used; an index out of range sets
+// kErrBounds and the access is skipped.  The release build defines it 0, and
+// the checks compile to nothing.
+#ifndef DSEA_CHECKED
+#define DSEA_CHECKED 0
+#endif
+
 namespace dsea {
 
 constexpr int kThreads = 256;            // threads per work-unit CTA
@@ -20,6 +29,7 @@ enum : int {
     kErrCapacity = 1,   // a cell or the shared-memory stage overflowed
     kErrMigration = 2,  // an atom left slices j-1..j+1 in one step
     kErrTimeout = 3,    // a bounded dependency wait expired
+    kErrBounds = 4,     // checked build: an index out of range (the access was skipped)
 };
 
 // One box as the kernels see it.  Slot layout: the state of a step lives in

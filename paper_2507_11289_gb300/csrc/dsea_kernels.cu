@@ -34,6 +34,21 @@ __device__ __forceinline__ void set_error(int *err, int code)
     atomicCAS(err, 0, code);
 }
 
+// Checked build (DSEA_CHECKED): whether 0 <= i < n, recording kErrBounds when
+// not, so that the caller skips the access.  Always true in the release build.
+__device__ __forceinline__ bool idx_ok(int *err, long long i, long long n)
+{
+#if DSEA_CHECKED
+    if (i < 0 || i >= n) {
+        set_error(err, kErrBounds);
+        return false;
+    }
+#else
+    (void)err; (void)i; (void)n;
+#endif
+    return true;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
     unsigned v;
@@ -395,6 +410,7 @@ __device__ __forceinline__ void store_f64(const BoxDev &B, int pn, long long slo
                                           double y, double z, double vx, double vy, double vz)
 {
     const long long S = B.n_slots;
+    if (!idx_ok(B.err, slot, S)) return;
     B.id[pn][slot] = aid;
     B.r[pn][slot] = x;
     B.r[pn][S + slot] = y;
@@ -412,6 +428,7 @@ __device__ __forceinline__ void store_mixed(const BoxDev &B, int pn, long long s
                                             float qy, float qz)
 {
     const long long S = B.n_slots;
+    if (!idx_ok(B.err, slot, S)) return;
     B.r[pn][slot] = x;
     B.r[pn][S + slot] = y;
     B.r[pn][2 * S + slot] = z;
@@ -534,7 +551,8 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         const int gy = wrap_index(y0 - 1 + ly, B.nc[1]);
         const int gz = wrap_index(z0 - 1 + lz, B.nc[2]);
         const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
-        const bool beyond = B.walls_x && (x0 - 1 + lx < 0 || x0 - 1 + lx >= B.nc[0]);   // past a wall
+        const bool beyond = (B.walls_x && (x0 - 1 + lx < 0 || x0 - 1 + lx >= B.nc[0])) ||   // past a wall
+                            !idx_ok(B.err, gc, B.n_cells);
         const unsigned long long ws = beyond ? 0ull : __ldcg(B.cnt[p] + gc);
         const unsigned long long wa = beyond ? 0ull : __ldcg(B.arr[p] + gc);
         int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;   // stayers (front)
@@ -694,6 +712,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             const bool own = lane < nin;
             long long slot = 0;
             if (own) slot = s_slot[is];
+            if (own && !idx_ok(B.err, slot, B.n_slots)) slot = 0;   // checked build: read a valid slot
             Acc64 a64 = {0.0, 0.0, 0.0, 0.0, 0.0};
             // The warp's scratch (32 x 5 doubles) holds, during the pair loop, the
             // pruned list of one neighbour cell (ints 0..127) and the chunk's
@@ -826,7 +845,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                     red_w += 0.5 * ww;
                     red_k += 0.5 * (sx * sx + sy * sy + sz * sz);
                     red_n += 1.0;
-                    if (!INTEGRATE) {
+                    if (!INTEGRATE && idx_ok(B.err, aid, B.n_atoms)) {
                         const long long o = 3LL * aid;
                         B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
                         B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
@@ -879,7 +898,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             __syncwarp();
         }
         // every home cell publishes how many atoms stayed in it, empty or not
-        if (INTEGRATE && lane == 0)
+        if (INTEGRATE && lane == 0 && idx_ok(B.err, hcell, B.n_cells))
             B.cnt[pn][hcell] = ((unsigned long long)tag_next << 32) | (unsigned long long)n_stay;
         if (thermo && lane == 0) {
             s_cellke[2 * h] = cell_ke;
@@ -901,9 +920,11 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 n += s_cellke[2 * q + 1];
             }
             const long long u = (long long)j * B.units_per_slice + tile;
-            B.th_part[p][2 * u] = ke;
-            B.th_part[p][2 * u + 1] = n;
-            B.th_lam[p][j] = lam;
+            if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
+                B.th_part[p][2 * u] = ke;
+                B.th_part[p][2 * u + 1] = n;
+                B.th_lam[p][j] = lam;
+            }
         }
     }
     if (OBS) {
@@ -929,10 +950,12 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                 k += s_red[q * 4 + 2];
                 n += s_red[q * 4 + 3];
             }
-            B.unit_obs[(long long)kObsStride * unit_id] = u;
-            B.unit_obs[(long long)kObsStride * unit_id + 1] = w;
-            B.unit_obs[(long long)kObsStride * unit_id + 2] = k;
-            B.unit_obs[(long long)kObsStride * unit_id + 3] = n;
+            if (idx_ok(B.err, unit_id, B.n_cells)) {
+                B.unit_obs[(long long)kObsStride * unit_id] = u;
+                B.unit_obs[(long long)kObsStride * unit_id + 1] = w;
+                B.unit_obs[(long long)kObsStride * unit_id + 2] = k;
+                B.unit_obs[(long long)kObsStride * unit_id + 3] = n;
+            }
         }
     }
 }
@@ -1031,7 +1054,8 @@ __device__ __forceinline__ NbrCell nbr_cell(const BoxDev &B, int p, unsigned tag
         const int gx = wrap_index(hx + ox, B.nc[0]), gy = wrap_index(hy + oy, B.nc[1]),
                   gz = wrap_index(hz + oz, B.nc[2]);
         const int gc = (gx * B.nc[1] + gy) * B.nc[2] + gz;
-        const unsigned long long ws = __ldcg(B.cnt[p] + gc), wa = __ldcg(B.arr[p] + gc);
+        const bool ok = idx_ok(B.err, gc, B.n_cells);
+        const unsigned long long ws = ok ? __ldcg(B.cnt[p] + gc) : 0ull, wa = ok ? __ldcg(B.arr[p] + gc) : 0ull;
         int n_s = ((unsigned)(ws >> 32) == tag) ? (int)(unsigned)ws : 0;
         int n_a = ((unsigned)(wa >> 32) == tag) ? (int)(unsigned)wa : 0;
         if (n_s + n_a > B.cap) {   // the two ends met: the cell overflowed
@@ -1082,8 +1106,9 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         // stayers: canonical position i = slot offset i
         const int lo = max(0, w0 - c.pre), hi = min(c.n_s, w1 - c.pre);
         for (int i = lo; i < hi; ++i) {
+            if (!idx_ok(B.err, c.pre + i - w0, kListAtoms) || !idx_ok(B.err, i, B.cap)) continue;
             cp_async16(&raw[c.pre + i - w0], q + base + i);
-            if (lane == 0) wa.hslot[i] = (unsigned char)i;
+            if (lane == 0 && idx_ok(B.err, i, kHomeMax)) wa.hslot[i] = (unsigned char)i;
         }
         // arrivals: slot cap-1-k holds the k-th arrival; order them by id
         const long long abase = base + B.cap - c.n_a;
@@ -1101,7 +1126,8 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
             const int cp = a0 + r;   // canonical list position
             if (cp >= w0 && cp < w1) {
                 raw[cp - w0] = a;
-                if (lane == 0) wa.hslot[c.n_s + r] = (unsigned char)(B.cap - c.n_a + t);
+                if (lane == 0 && idx_ok(B.err, c.n_s + r, kHomeMax))
+                    wa.hslot[c.n_s + r] = (unsigned char)(B.cap - c.n_a + t);
             }
         }
         // padding: after an odd home cell, and after an odd list
@@ -1180,12 +1206,12 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         const bool ka = load_test(e0 + lane, a), kb = load_test(e0 + 32 + lane, b);
         const unsigned kA = __ballot_sync(kFull, ka), kB = __ballot_sync(kFull, kb);
         __syncwarp();
-        if (ka) {
+        if (ka && idx_ok(B.err, m + __popc(kA & below), kListAtoms)) {
             float *d = list_entry(wa, m + __popc(kA & below));
             d[0] = a.x; d[2] = a.y; d[4] = a.z; d[6] = a.w;
         }
         m += __popc(kA);
-        if (kb) {
+        if (kb && idx_ok(B.err, m + __popc(kB & below), kListAtoms)) {
             float *d = list_entry(wa, m + __popc(kB & below));
             d[0] = b.x; d[2] = b.y; d[4] = b.z; d[6] = b.w;
         }
@@ -1332,7 +1358,8 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
     double rr[3] = {0.0, 0.0, 0.0};
     float vv[3] = {0.f, 0.f, 0.f};
     if (own) {
-        slot = v.hcell * B.cap + wa.hslot[ib + lane];
+        slot = v.hcell * B.cap + (idx_ok(B.err, ib + lane, kHomeMax) ? wa.hslot[ib + lane] : 0);
+        if (!idx_ok(B.err, slot, B.n_slots)) slot = 0;   // checked build: read a valid slot
         if (v.total <= kListAtoms) {
             const float *f = list_entry(wa, ib + lane);
             qo = make_float4(f[0], f[2], f[4], f[6]);
@@ -1353,7 +1380,7 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
             red.w += 0.5 * (double)ww;
             red.k += 0.5 * (double)fmaf(sx, sx, fmaf(sy, sy, sz * sz));
             red.n += 1.0;
-            if (!INTEGRATE) {   // absolute positions: the home cell's centre plus the relative one
+            if (!INTEGRATE && idx_ok(B.err, aid, B.n_atoms)) {   // absolute: cell centre plus relative
                 const long long o = 3LL * aid;
                 B.out_f[o] = fx; B.out_f[o + 1] = fy; B.out_f[o + 2] = fz;
                 B.out_v[o] = sx; B.out_v[o + 1] = sy; B.out_v[o + 2] = sz;
@@ -1443,7 +1470,7 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, O
         home_update<INTEGRATE, OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww, red);
     }
     // the home cell publishes how many atoms stayed in it, empty or not
-    if (INTEGRATE && lane == 0)
+    if (INTEGRATE && lane == 0 && idx_ok(B.err, v.hcell, B.n_cells))
         B.cnt[(int)(v.s_abs & 1) ^ 1][v.hcell] = ((unsigned long long)(unsigned)(v.s_abs + 2) << 32) |
                                                   (unsigned long long)(unsigned)v.n_stay;
     __syncwarp();   // the list and slot table are reused by the next home cell
@@ -1476,9 +1503,11 @@ __device__ __forceinline__ void mixed_unit_end(const BoxDev &B, WarpArea &wa, in
     if (lane == 0) {
         const int p = (int)(s_abs & 1);
         const long long u = (long long)j * B.units_per_slice + tile;
-        B.th_part[p][2 * u] = wa.ke_acc;
-        B.th_part[p][2 * u + 1] = wa.n_acc;
-        B.th_lam[p][j] = wa.lam;
+        if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
+            B.th_part[p][2 * u] = wa.ke_acc;
+            B.th_part[p][2 * u + 1] = wa.n_acc;
+            B.th_lam[p][j] = wa.lam;
+        }
     }
 }
 
@@ -1695,7 +1724,7 @@ __global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long
             red.k += __shfl_xor_sync(kFull, red.k, o);
             red.n += __shfl_xor_sync(kFull, red.n, o);
         }
-        if (lane == 0) {
+        if (lane == 0 && idx_ok(sB.err, u, sB.n_cells)) {
             sB.unit_obs[(long long)kObsStride * u] = red.u;
             sB.unit_obs[(long long)kObsStride * u + 1] = red.w;
             sB.unit_obs[(long long)kObsStride * u + 2] = red.k;
@@ -1784,6 +1813,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(Rin
                 }
                 const int m = (int)(r - plan.cum_units[bl]);
                 const int ups = sB.units_per_slice;
+                idx_ok(sB.err, m, (long long)sB.n_slices * ups);   // checked build: a bad unit fails the box
                 const int jj = m / ups;
                 const int j = ring_slice(jj, sB.step + s_rel, sB.n_slices);
                 s_dec[0] = s_rel;
@@ -1797,6 +1827,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(Rin
                     for (int d = -2; d <= 2 && go == 1; ++d) {
                         if (sB.walls_x && (j + d < 0 || j + d >= sB.n_slices)) continue;   // no slice past a wall
                         const int k = wrap_index(j + d, sB.n_slices);
+                        if (!idx_ok(sB.err, k, sB.n_slices)) continue;
                         unsigned sleep = 32;
                         while (ld_acquire(sB.done + k) < need) {
                             if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
@@ -1822,7 +1853,8 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(Rin
             run_unit_f64<true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
         __threadfence();
         __syncthreads();
-        if (tid == 0 && !(j == sB.withhold_slice && s_rel == 0)) atomicAdd(sB.done + j, 1u);
+        if (tid == 0 && !(j == sB.withhold_slice && s_rel == 0) && idx_ok(sB.err, j, sB.n_slices))
+            atomicAdd(sB.done + j, 1u);
     }
 }
 
@@ -1882,6 +1914,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
             const int s_rel = wa.rel;
             const int m = (int)(r - plan.cum_units[bl]);
             const int ups = B.units_per_slice;
+            idx_ok(B.err, m, (long long)B.n_slices * ups);   // checked build: a bad unit fails the box
             const int jj = m / ups;
             const int j = ring_slice(jj, B.step + s_rel, B.n_slices);
             wa.j = j;
@@ -1896,6 +1929,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
                 for (int d = -2; d <= 2 && go == 1; ++d) {
                     if (B.walls_x && (j + d < 0 || j + d >= B.n_slices)) continue;   // no slice past a wall
                     const int k = wrap_index(j + d, B.n_slices);
+                    if (!idx_ok(B.err, k, B.n_slices)) continue;
                     unsigned sleep = 32;
                     while (ld_acquire(B.done + k) < need) {
                         if (ld_volatile_int(plan.err) != 0) { go = 0; break; }
@@ -1926,7 +1960,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
         __syncwarp();
         if (lane == 0) {
             const int j = v.j;
-            if (!(j == B.withhold_slice && v.rel == 0)) atomicAdd(B.done + j, 1u);
+            if (!(j == B.withhold_slice && v.rel == 0) && idx_ok(B.err, j, B.n_slices)) atomicAdd(B.done + j, 1u);
         }
     }
 }

@@ -28,6 +28,7 @@ ERR_STATE = -8
 ERR_NOT_FOUND = -9
 ERR_NO_DEVICE = -10
 ERR_SCRATCH_LIMIT = -11
+ERR_BOUNDS = -12           # checked build only: a kernel met an index out of range
 
 FP64 = 0
 MIXED = 1
@@ -130,12 +131,20 @@ _lib = None
 _lock = threading.Lock()
 
 
+def checked_variant() -> bool:
+    """Whether the process loads the bounds-checked library: environment
+    variable DSEA_VARIANT=checked, read when the library is first loaded."""
+    return os.environ.get("DSEA_VARIANT", "") == "checked"
+
+
 def library_path() -> str:
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libdsea.so")
+    name = "libdsea_checked.so" if checked_variant() else "libdsea.so"
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", name)
 
 
 def load(build: bool = True):
-    """Load libdsea.so (building it in-tree first if stale and nvcc exists)."""
+    """Load libdsea.so (building it in-tree first if stale and nvcc exists);
+    libdsea_checked.so instead under DSEA_VARIANT=checked."""
     global _lib
     with _lock:
         if _lib is None:
@@ -143,7 +152,7 @@ def load(build: bool = True):
             if build:
                 from . import build as _build
                 try:
-                    path = _build.build()
+                    path = _build.build(checked=checked_variant())
                 except RuntimeError:
                     if not os.path.exists(path):
                         raise

@@ -29,9 +29,22 @@ def test_library_exports_every_declared_call():
     assert set(dsea._SIGS) == set(names)
 
 
+def test_checked_variant_builds_and_exports_the_same_calls():
+    """The bounds-checked build (-DDSEA_CHECKED=1) is the same ABI."""
+    import ctypes
+
+    from paper_2507_11289_gb300 import build
+    lib = ctypes.CDLL(build.build(checked=True))
+    for name in _declared():
+        assert hasattr(lib, name), name
+    fn = lib.dsea_status_string
+    fn.restype, fn.argtypes = ctypes.c_char_p, [ctypes.c_int]
+    assert fn(dsea.ERR_BOUNDS) == b"index out of range (checked build)"
+
+
 def test_status_strings_and_version():
     assert dsea.version() == "0.1.0"
-    for code in range(-10, 1):
+    for code in range(-12, 1):
         s = dsea.status_string(code)
         assert s and s != "unknown status"
     assert dsea.status_string(-99) == "unknown status"
