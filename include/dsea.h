@@ -85,7 +85,12 @@ typedef struct {
     int tile_z;        /* home cells per work unit along z */
     int cell_capacity; /* atom slots per cell; 0 = from the density */
     int ctas;          /* CTAs of a ring launch (one stage each in the FP64 form, one per
-                          warp in the mixed form); 0 = all that fit */
+                          warp in the mixed form); 0 = automatic: the autotuner's choice
+                          for the size class when it has one, else in the mixed form
+                          n_slices x min(units per slice, 160) warps (all resident CTAs
+                          when that is at least 90 % of them), in the FP64 form all
+                          resident CTAs.  Launches of several boxes (batches, the
+                          server) use the mixed rule summed over their boxes. */
     double temperature; /* NVT: target kT/epsilon of the slice thermostat (Sec. 4.1,
                            md_thermo_a/b and md_v3b); 0 = NVE.  Each step scales the
                            synchronised velocities of slice j by sqrt(T0 / T'_j), T'_j
@@ -224,12 +229,16 @@ int dsea_batch_destroy(dsea_batch *batch);
 
 /* ---- autotuning -------------------------------------------------------- */
 
-/* Time each candidate work-unit shape (tile_y x tile_z home cells) for
- * trial_steps steps from a snapshot of the box's state (taken through the
- * box's allocator, restored after each trial) and keep the fastest; the
- * choice is cached per size class (cells along y and z up to 16, cell layers
- * per slice, cell capacity, precision), applied to the box and used as the
- * default shape of later boxes of the same class.  The tile shape never
+/* Time each candidate work-unit shape (tile_y x tile_z home cells), then at
+ * the fastest shape each ring stage count (all resident CTAs, 3/4, 1/2 and
+ * 1/4 of them, against the default rule), for trial_steps steps each from a
+ * snapshot of the box's state (taken through the box's allocator, restored
+ * after each trial), and keep the fastest; a fixed stage count is kept only
+ * when it is at least 3 % faster than the default.  The choice is cached per
+ * size class (total cells and mean atoms per cell in octaves, cells along y
+ * and z up to 16, cell layers per slice, cell capacity, precision), applied
+ * to the box and used as the default shape and stage count of later boxes of
+ * the same class.  The tile shape never
  * changes a result: each atom's force is summed in the same order whatever
  * the shape.  *chosen (may be NULL) receives the parameters in effect. */
 int dsea_autotune(dsea_box *box, int trial_steps, dsea_params *chosen);

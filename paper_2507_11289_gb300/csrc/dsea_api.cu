@@ -125,6 +125,28 @@ int num_sms()
     return n > 0 ? n : 1;
 }
 
+// Stages (CTAs) of a mixed-form ring launch when the caller leaves the count
+// to the library.  A slice's units at one level can only run while its
+// neighbours' previous level completes, so only about kSliceWarps units of a
+// slice run at once usefully.  More warps mostly wait: measured on lone
+// boxes of 32k-187k atoms, all 608 resident CTAs ran 20-38 % slower than
+// n_slices x min(units per slice, 160) warps, while from 296k atoms on, all
+// stages were as fast or faster.  The launch uses all resident stages unless
+// the rule asks for at most 90 % of them.  `want_warps` is the rule summed
+// over the launch's boxes; `full` the resident count.
+constexpr int kSliceWarps = 160;
+
+int64_t slice_rule_warps(const BoxDev &hb)
+{
+    return (int64_t)hb.n_slices * std::min<int64_t>(hb.units_per_slice, kSliceWarps);
+}
+
+int mixed_ring_ctas(int64_t want_warps, int full)
+{
+    const int64_t want = (want_warps + dsea::kWarps - 1) / dsea::kWarps;
+    return want < (int64_t)(0.9 * full) ? (int)std::max<int64_t>(want, 1) : full;
+}
+
 // Fill the work-unit shape fields of hb for a (ty, tz) tile.
 bool apply_tile(BoxDev &hb, double mean_cap, int ty, int tz)
 {
@@ -253,7 +275,10 @@ int ring_launch_single(dsea_box *b, int64_t n)
     plan.err = b->d_launch_err;
     const size_t smem = dsea::unit_smem_bytes(hb.precision, hb.staged_cells, hb.smem_atoms);
     int ctas = b->params.ctas;
-    if (ctas <= 0) ctas = num_sms() * std::max(1, dsea::ring_ctas_per_sm(hb.precision, smem));
+    if (ctas <= 0) {
+        ctas = num_sms() * std::max(1, dsea::ring_ctas_per_sm(hb.precision, smem));
+        if (hb.precision == DSEA_MIXED) ctas = mixed_ring_ctas(slice_rule_warps(hb), ctas);
+    }
     if ((int64_t)ctas > plan.total) ctas = (int)plan.total;
     CU(dsea::launch_ring(plan, hb.precision, smem, ctas, b->stream));
     return DSEA_OK;
@@ -416,7 +441,12 @@ struct BoxSnapshot {
 };
 
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+// What the autotuner chose for a size class: the unit shape and the ring's
+// stage count (0: the default rule).
+struct TuneChoice {
+    int ty, tz, ctas;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
 
 // Geometry, cell capacity, pair constants and work-unit shape of a box
 // (Sec. 4: slices along x of width >= rc, cells of edge >= rc); validates p
@@ -505,8 +535,9 @@ int setup_geometry(int n_slices_req, const double *L, int64_t n_atoms, dsea_para
         std::unique_lock<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(size_class(hb.nc, cps, cap, p.precision, n_atoms));
         if (it != g_tune_cache.end()) {
-            ty = it->second.first;
-            tz = it->second.second;
+            ty = it->second.ty;
+            tz = it->second.tz;
+            if (p.ctas == 0) p.ctas = it->second.ctas;
         } else if (p.precision == DSEA_MIXED) {
             lk.unlock();
             const int ci = pick_filling_shape(
@@ -895,13 +926,14 @@ int dsea_batch_advance(dsea_batch *bt, const int64_t *steps)
     }
     int rc = dsea::multi_prepare(bt->mp, bt->boxes.data(), steps, n);
     if (rc) return rc;
-    std::vector<int64_t> key(2 * n + 2);
+    std::vector<int64_t> key(2 * n + 3);
     for (int k = 0; k < n; ++k) {
         key[k] = bt->mp.order[k];
         key[n + k] = steps[bt->mp.order[k]];
     }
     key[2 * n] = (int64_t)bt->mp.smem;
     key[2 * n + 1] = bt->mp.total;   // the grid is sized by the units of the whole run
+    key[2 * n + 2] = bt->mp.want_warps;   // and by the stage-count rule
     auto it = bt->graphs.find(key);
     if (it == bt->graphs.end()) {
         cudaStream_t st = bt->stream;
@@ -958,7 +990,7 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
     if (rc) return rc;
     BoxDev &hb = b->hb;
     const TuneKey key = size_class(hb.nc, hb.cps, hb.cap, hb.precision, hb.n_atoms);
-    std::pair<int, int> best{hb.tile_y, hb.tile_z};
+    TuneChoice best{hb.tile_y, hb.tile_z, b->params.ctas};
     bool cached = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -972,42 +1004,75 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         BoxSnapshot snap;
         rc = snap.save(b);
         if (rc) return rc;
-        // candidate unit shapes: mixed units are one warp's, FP64 units one CTA's
-        static const int cand_mixed[][2] = {{1, 2}, {2, 2}, {1, 4}, {2, 4}, {3, 3}, {4, 4}};
-        static const int cand_f64[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
-        const bool tune_mixed = hb.precision == 1;
-        const int n_cand = tune_mixed ? 6 : 8;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        float best_ms = 1e30f;
         const int sched = b->params.schedule;
+        const int ctas0 = b->params.ctas;
         const BoxDev saved = hb;
-        for (int ci = 0; ci < n_cand; ++ci) {
-            const int *c = tune_mixed ? cand_mixed[ci] : cand_f64[ci];
-            BoxDev trial = saved;
-            if (!apply_tile(trial, b->mean_cap, c[0], c[1])) continue;
-            if (trial.tile_y != c[0] || trial.tile_z != c[1]) continue;   // clipped duplicate
-            hb = trial;
-            b->params.schedule = DSEA_SCHED_RING;
-            rc = advance_impl(b, 1);   // warm-up
-            if (!rc) {
+        b->params.schedule = DSEA_SCHED_RING;
+        // one trial: a warm-up step, then trial_steps timed, then the state restored
+        auto trial = [&](const BoxDev &shape, int ctas, float &ms) -> int {
+            hb = shape;
+            b->params.ctas = ctas;
+            int r = advance_impl(b, 1);
+            if (!r) {
                 cudaEventRecord(e0, b->stream);
-                rc = advance_impl(b, trial_steps);
+                r = advance_impl(b, trial_steps);
                 cudaEventRecord(e1, b->stream);
             }
-            if (!rc) rc = check_device_error(b);
+            if (!r) r = check_device_error(b);
+            ms = 0;
+            if (!r) cudaEventElapsedTime(&ms, e0, e1);
+            const int rr = snap.restore();
+            return r ? r : rr;
+        };
+        // 1. the unit shape (mixed units are one warp's, FP64 units one CTA's),
+        //    at the default stage count
+        static const int cand_mixed[][2] = {{1, 2}, {2, 2}, {1, 4}, {2, 4}, {3, 3}, {4, 4}};
+        static const int cand_f64[][2] = {{2, 2}, {2, 4}, {3, 3}, {4, 4}, {4, 8}, {8, 4}, {6, 6}, {8, 8}};
+        const bool tune_mixed = hb.precision == DSEA_MIXED;
+        const int n_cand = tune_mixed ? 6 : 8;
+        float best_ms = 1e30f;
+        BoxDev best_shape = saved;
+        for (int ci = 0; ci < n_cand && !rc; ++ci) {
+            const int *c = tune_mixed ? cand_mixed[ci] : cand_f64[ci];
+            BoxDev t = saved;
+            if (!apply_tile(t, b->mean_cap, c[0], c[1])) continue;
+            if (t.tile_y != c[0] || t.tile_z != c[1]) continue;   // clipped duplicate
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const int rrc = snap.restore();
-            if (!rc) rc = rrc;
-            if (rc) break;
-            if (ms < best_ms) {
+            rc = trial(t, 0, ms);
+            if (!rc && ms < best_ms) {
                 best_ms = ms;
-                best = {trial.tile_y, trial.tile_z};
+                best_shape = t;
+                best = {t.tile_y, t.tile_z, 0};
+            }
+        }
+        // 2. the stage count at that shape: all resident stages and fractions
+        //    of them against the default rule (0)
+        if (!rc) {
+            const size_t smem = dsea::unit_smem_bytes(best_shape.precision, best_shape.staged_cells,
+                                                      best_shape.smem_atoms);
+            const int full = num_sms() * std::max(1, dsea::ring_ctas_per_sm(best_shape.precision, smem));
+            int tried[5] = {0, 0, 0, 0, 0};
+            int n_tried = 0;
+            for (int q : {4, 3, 2, 1}) {
+                const int c = std::max(1, full * q / 4);
+                bool dup = false;
+                for (int k = 0; k < n_tried; ++k) dup = dup || tried[k] == c;
+                if (dup) continue;
+                tried[n_tried++] = c;
+                float ms = 0;
+                rc = trial(best_shape, c, ms);
+                if (rc) break;
+                if (ms < 0.97f * best_ms) {   // a fixed count must beat the default clearly
+                    best_ms = ms;
+                    best.ctas = c;
+                }
             }
         }
         b->params.schedule = sched;
+        b->params.ctas = ctas0;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaStreamSynchronize(b->stream);
@@ -1017,9 +1082,10 @@ int dsea_autotune(dsea_box *b, int trial_steps, dsea_params *chosen)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    apply_tile(hb, b->mean_cap, best.first, best.second);
+    apply_tile(hb, b->mean_cap, best.ty, best.tz);
     b->params.tile_y = hb.tile_y;
     b->params.tile_z = hb.tile_z;
+    b->params.ctas = best.ctas;
     b->tile_auto = false;
     b->outputs_valid = false;
     if (chosen) *chosen = b->params;
@@ -1208,12 +1274,14 @@ int multi_prepare(MultiPlan &mp, dsea_box *const *boxes, const int64_t *steps, i
     std::stable_sort(mp.order.begin(), mp.order.end(),
                      [&](int a, int c) { return steps[a] > steps[c]; });
     mp.smem = 0;
+    mp.want_warps = 0;
     mp.precision = n > 0 ? boxes[0]->hb.precision : 0;
     mp.h_cum[0] = 0;
     for (int k = 0; k < n; ++k) {
         dsea_box *b = boxes[mp.order[k]];
         if (b->hb.precision != mp.precision) return DSEA_ERR_INVALID_ARG;
         mp.h_boxes[k] = b->hb;
+        mp.want_warps += slice_rule_warps(b->hb);
         mp.h_cum[k + 1] = mp.h_cum[k] + (int64_t)b->hb.n_slices * b->hb.units_per_slice;
         mp.smem = std::max(mp.smem, unit_smem_bytes(b->hb.precision, b->hb.staged_cells, b->hb.smem_atoms));
     }
@@ -1256,6 +1324,7 @@ int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t st)
     plan.ticket = mp.d_ticket;
     plan.err = mp.d_err;
     int ctas = num_sms() * std::max(1, ring_ctas_per_sm(mp.precision, mp.smem));
+    if (mp.precision == DSEA_MIXED) ctas = mixed_ring_ctas(mp.want_warps, ctas);
     if ((int64_t)ctas > mp.total) ctas = (int)mp.total;
     CU(launch_ring(plan, mp.precision, mp.smem, ctas, st));
     return DSEA_OK;

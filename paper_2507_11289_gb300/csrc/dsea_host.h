@@ -71,6 +71,7 @@ struct MultiPlan {
     int64_t smax = 0, total = 0;
     size_t smem = 0;
     int precision = 0;
+    int64_t want_warps = 0;   // mixed form: the stage-count rule summed over the boxes
     std::vector<int> order;
 };
 

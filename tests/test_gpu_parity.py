@@ -118,6 +118,27 @@ def test_unit_shape_does_not_change_results(melted_4k):
         assert np.array_equal(r, ref), (ty, tz)
 
 
+@pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
+def test_stage_count_does_not_change_results(precision):
+    """The ring's stage count (CTAs of the persistent launch) only changes
+    which stage takes which unit: one CTA, a few, the default rule and every
+    resident CTA give the same bits on a 62,500-atom box (17 slices, where
+    the default rule runs about half the resident stages)."""
+    import torch
+    pos, box = inputs.fcc_lattice(25, 0.8)
+    vel = inputs.maxwell_boltzmann(len(pos), 1.5, 8)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ref = None
+    for ctas in (1, 3, 0, sms * (4 if precision == dsea.MIXED else 2)):
+        with dsea.Box(pos, vel, box, precision=precision, ctas=ctas) as b:
+            b.advance(12 if precision == dsea.MIXED else 4)
+            got = (b.positions(), b.velocities(), b.observables())
+        if ref is None:
+            ref = got
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), ctas
+        assert got[2] == ref[2], ctas
+
+
 @pytest.mark.parametrize("n_slices", [3, 4, 6])
 def test_slice_count_fp64_parity(n_slices, melted_4k):
     pos, vel, box = melted_4k
