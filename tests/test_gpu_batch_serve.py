@@ -280,3 +280,67 @@ print(json.dumps(out))
     assert e["tile"] == e["untuned"], out                          # not the dilute box's choice
     assert g["cap"] == e["cap"] and min(g["cells"][1:]) >= 16 and min(e["cells"][1:]) >= 16
     assert g["tile"] == g["untuned"], out                          # not the 17^3 box's choice
+
+
+def _force_err(Fg, Fo):
+    rms = lambda a: float(np.sqrt((np.asarray(a) ** 2).sum(-1).mean()))
+    return rms(Fg - Fo) / rms(Fo)
+
+
+def test_full_512_box_batch_sampled_boxes():
+    """The batch as the benchmark runs it: the 512 boxes (500-50,000 atoms,
+    rho 0.05-0.9, T 0.7-3.0), one unit shape from the batch autotuner, one
+    graph-replayed launch.  After 20 steps, 8 sampled boxes hold their runs
+    alone bit for bit, and their forces are the oracle's at the GPU's
+    positions within the mixed form's per-step gate (rms 2e-6 of the rms
+    force)."""
+    specs = inputs.batch_specs(n_boxes=512, steps=20)
+    states = [s.state() for s in specs]
+    boxes = [dsea.Box(*st, precision=dsea.MIXED) for st in states]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        dsea.batch_autotune(bt, trial_steps=2)
+        dsea.batch_advance(bt, [20] * len(boxes))
+        dsea.batch_destroy(bt)
+        rng = np.random.default_rng(5)
+        for k in sorted(rng.choice(len(boxes), 8, replace=False)):
+            r, v, f = boxes[k].positions(), boxes[k].velocities(), boxes[k].forces()
+            ra, va, _ = _alone(states[k], 20)
+            assert np.array_equal(r, ra) and np.array_equal(v, va), k
+            Fo, _, _ = oracle.forces(r, states[k][2], 2.5, "cells")
+            e = _force_err(f, Fo)
+            print(f"box {k}: {len(r)} atoms, rho {specs[k].rho:.2f}, force error rms {e:.2e}")
+            assert e <= 2e-6, (k, e)
+    finally:
+        for b in boxes:
+            b.close()
+
+
+def test_served_stream_sampled_jobs_equal_alone():
+    """The served stream as the benchmark draws it (Poisson 200 jobs/s, N
+    log-uniform 1e3-2e6, rho 0.3-0.9, T 0.8-2.5; 60 GB budget, 100-step
+    segments): its first 24 jobs, submitted at their arrival times with their
+    step counts capped at 300, run overlapped on the device; 4 sampled jobs
+    end bit for bit where they end alone."""
+    jobs = inputs.served_stream(rate_per_s=200.0, duration_s=1.0)[:24]
+    steps = [min(j.spec.steps, 300) for j in jobs]
+    states = [j.spec.state() for j in jobs]
+    srv = dsea.server_create(60 << 30, dsea.make_params(precision=dsea.MIXED), 100, 0)
+    try:
+        t0 = time.perf_counter()
+        ids = []
+        for j, st, n in zip(jobs, states, steps):
+            wait = j.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(dsea.server_submit(srv, *st, n))
+        dsea.server_drain(srv)
+        rng = np.random.default_rng(9)
+        for k in sorted(rng.choice(len(jobs), 4, replace=False)):
+            assert dsea.server_poll(srv, ids[k]) == 2
+            r, v, o, _, _ = dsea.server_result(srv, ids[k], len(states[k][0]))
+            ra, va, oa = _alone(states[k], steps[k])
+            print(f"job {k}: {len(r)} atoms, {steps[k]} steps")
+            assert np.array_equal(r, ra) and np.array_equal(v, va) and o == oa, k
+    finally:
+        dsea.server_destroy(srv)
