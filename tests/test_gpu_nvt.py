@@ -42,6 +42,32 @@ def test_fp64_nvt_trajectory_matches_oracle(melted_4k):
     assert og["KE"] == pytest.approx(obs[-1, 2], rel=1e-10)
 
 
+def test_fp64_nvt_with_walls_matches_oracle(melted_4k):
+    """The slice thermostat and mirror walls together (the paper's validation
+    runs combine its thermostat with the walls at the x ends): 100 FP64
+    steps against the oracle's, then the per-slice profiles."""
+    pos, vel, box = melted_4k
+    T0 = 1.3
+    with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.FP64, temperature=T0, walls=True) as b:
+        ncx, cps = slices_of(b)
+        b.advance(60)
+        b.advance(40)
+        rg, vg, og = b.positions(), b.velocities(), b.observables()
+        pg = b.profiles()
+    ro, vo, Fo, obs, st = oracle.run_nvt(pos, vel, box, 100, ncx, cps, T0, walls=True)
+    assert rg[:, 0].min() >= 0.0 and rg[:, 0].max() < box[0]   # nothing crossed a wall
+    d = rg - ro                       # no periodic image along x; y and z stay periodic
+    d[:, 1:] = min_image(d[:, 1:], box[1:])
+    dr = np.abs(d).max()
+    dv = np.abs(vg - vo).max()
+    print(f"NVT + walls FP64: max |dr| {dr:.3e}, max |dv| {dv:.3e}")
+    assert dr <= 1e-9 and dv <= 1e-8
+    assert og["KE"] == pytest.approx(obs[-1, 2], rel=1e-10)
+    po = oracle.profiles(rg, vg, box, ncx, cps, walls=True)
+    assert np.array_equal(pg["N"], po[:, 3].astype(np.int64))
+    assert np.allclose(pg["KE"], po[:, 2], rtol=1e-10)
+
+
 @pytest.mark.parametrize("precision,tol", [(dsea.FP64, 1e-13), (dsea.MIXED, 1e-6)])
 def test_ideal_gas_slices_reach_the_target_in_one_scaling(precision, tol):
     temps = [2.0, 0.5, 1.2]

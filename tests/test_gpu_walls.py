@@ -122,3 +122,31 @@ def test_mixed_energy_drift_with_walls_1000_steps(melted_4k):
     drift_ora = abs(e_ora[-10:].mean() - e_ora[:10].mean())
     print(f"walls: drift per atom over 1000 steps: mixed {drift_gpu:.3e}, oracle FP64 {drift_ora:.3e}")
     assert drift_gpu <= max(1e-4, 2.0 * drift_ora)
+
+
+@pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
+def test_walls_box_in_a_batch_equals_alone(precision, melted_4k):
+    """A box with mirror walls and periodic boxes in one persistent launch:
+    each box keeps its own boundary, and ends bit for bit where it ends
+    alone."""
+    pos, vel, box = melted_4k
+    others = [s.state() for s in inputs.batch_specs(n_boxes=2, seed=12, n_max=5000)]
+    kinds = [((pos, vel, box), True), (others[0], False), (others[1], False)]
+    steps = [25, 18, 25]
+    alone = []
+    for (st, walls), n in zip(kinds, steps):
+        with dsea.Box(*st, n_slices=4 if walls else 0, precision=precision, walls=walls) as b:
+            b.advance(n)
+            alone.append((b.positions(), b.velocities(), b.observables()))
+    boxes = [dsea.Box(*st, n_slices=4 if walls else 0, precision=precision, walls=walls) for st, walls in kinds]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        dsea.batch_advance(bt, steps)
+        dsea.batch_destroy(bt)
+        for b, (r, v, o) in zip(boxes, alone):
+            assert np.array_equal(b.positions(), r) and np.array_equal(b.velocities(), v)
+            assert b.observables() == o
+        assert np.all((boxes[0].positions()[:, 0] >= 0) & (boxes[0].positions()[:, 0] < box[0]))
+    finally:
+        for b in boxes:
+            b.close()
