@@ -344,3 +344,23 @@ def test_served_stream_sampled_jobs_equal_alone():
             assert np.array_equal(r, ra) and np.array_equal(v, va) and o == oa, k
     finally:
         dsea.server_destroy(srv)
+
+
+def test_server_with_thermostat_jobs_equal_alone():
+    """A server whose params set the slice thermostat runs every job under it;
+    each job ends bit for bit where it ends alone with the same params."""
+    states = _boxes(3, seed=14)
+    steps = [30, 12, 21]
+    params = dsea.make_params(precision=dsea.MIXED, temperature=1.1)
+    srv = dsea.server_create(8 << 30, params, 10, 0)
+    try:
+        ids = [dsea.server_submit(srv, *st, n) for st, n in zip(states, steps)]
+        dsea.server_drain(srv)
+        for jid, st, n in zip(ids, states, steps):
+            r, v, o, _, _ = dsea.server_result(srv, jid, len(st[0]))
+            with dsea.Box(*st, precision=dsea.MIXED, temperature=1.1) as b:
+                b.advance(n)
+                assert np.array_equal(r, b.positions()) and np.array_equal(v, b.velocities())
+                assert o == b.observables()
+    finally:
+        dsea.server_destroy(srv)

@@ -136,3 +136,32 @@ def test_profiles_match_oracle(precision, melted_4k):
         po = oracle.profiles(rg, vg, box, ncx, cps)
         assert np.array_equal(pg["N"], po[:, 3].astype(np.int64))
         assert np.allclose(pg["U"], po[:, 0], rtol=1e-11)
+
+
+@pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
+def test_thermostat_box_in_a_batch_equals_alone(precision, melted_4k):
+    """A box under the slice thermostat beside an NVE box in one persistent
+    launch: each keeps its own ensemble and ends bit for bit where it ends
+    alone (slice factors are per box and per step parity)."""
+    pos, vel, box = melted_4k
+    other = inputs.batch_specs(n_boxes=1, seed=21, n_max=5000)[0].state()
+    kinds = [((pos, vel, box), 1.2, 4), (other, 0.0, 0)]
+    steps = [30, 21]
+    alone = []
+    for (st, T0, ns), n in zip(kinds, steps):
+        with dsea.Box(*st, n_slices=ns, precision=precision, temperature=T0) as b:
+            b.advance(n)
+            alone.append((b.positions(), b.velocities(), b.observables(), b.profiles()))
+    boxes = [dsea.Box(*st, n_slices=ns, precision=precision, temperature=T0) for st, T0, ns in kinds]
+    try:
+        bt = dsea.batch_create([b.h for b in boxes])
+        dsea.batch_advance(bt, steps)
+        dsea.batch_destroy(bt)
+        for b, (r, v, o, p) in zip(boxes, alone):
+            assert np.array_equal(b.positions(), r) and np.array_equal(b.velocities(), v)
+            assert b.observables() == o
+            q = b.profiles()
+            assert all(np.array_equal(q[k], p[k]) for k in p)
+    finally:
+        for b in boxes:
+            b.close()
