@@ -309,7 +309,8 @@ int oracle_forces_subset_w(int64_t n, const double *pos, const double *box, doub
     double rc2 = rc * rc, ushift = lj_shift(rc);
     for (int64_t k = 0; k < m; ++k) {
         double uh, wh;
-        atom_from_cells(idx[k], pos, box, rc2, ushift, walls_x, &cl, &F[3 * k], &uh, &wh);
+        const int64_t i = ORACLE_MUTANT == 14 ? (idx[k] + 1) % n : idx[k];
+        atom_from_cells(i, pos, box, rc2, ushift, walls_x, &cl, &F[3 * k], &uh, &wh);
         if (u_atom) u_atom[k] = uh;
         if (w_atom) w_atom[k] = wh;
     }
@@ -402,7 +403,8 @@ static void slice_thermostat(int64_t n, const double *pos, double *vel, const do
     for (int j = 0; j < ns; ++j) {
         double ke = prev[2 * j], cnt = prev[2 * j + 1];
         double ke_after = (ORACLE_MUTANT == 11 ? 1.0 : lam[j] * lam[j]) * ke;
-        lam[j] = (cnt > 0.0 && ke_after > 0.0) ? sqrt(T0 * 3.0 * cnt / (2.0 * ke_after)) : 1.0;
+        const double ratio = T0 * 3.0 * cnt / (2.0 * ke_after);
+        lam[j] = (cnt > 0.0 && ke_after > 0.0) ? (ORACLE_MUTANT == 13 ? ratio : sqrt(ratio)) : 1.0;
     }
     for (int64_t i = 0; i < n; ++i) {
         int j = slice_of(pos[3 * i], box[0], nc_x, cps);

@@ -9,8 +9,10 @@ layer of neighbour cells, a dropped term of the velocity update, a dropped
 term of the position update, a virial without its r^2 factor, a strict
 cutoff instead of the inclusive one, a mirror wall that reflects positions but
 not velocities, pairs that still meet across the mirror walls, a thermostat
-that forgets its own previous scaling, and slice profiles that count whole
-pair energies.
+that forgets its own previous scaling, a thermostat factor without its
+square root, slice profiles that count whole pair energies, and a subset
+force call (the one behind the full-size sampled parity tests) that
+evaluates the neighbouring atom instead of the one asked for.
 """
 import os
 
@@ -34,6 +36,8 @@ CASES = {
     10: [walls.test_no_pair_across_the_walls],
     11: [nvt.test_ideal_gas_reaches_the_target_in_one_scaling],
     12: [lambda: nvt.test_fcc_profiles_are_the_lattice_sums()],
+    13: [nvt.test_ideal_gas_reaches_the_target_in_one_scaling],
+    14: [pins.test_subset_matches_full],
 }
 
 
