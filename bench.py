@@ -263,22 +263,26 @@ def e2e_run(dsea, torch, spec, precision, steps, md_steps, stream):
             "d2h_bytes_per_step": int(out_r.nbytes + out_v.nbytes)}
 
 
-def batch_run(dsea, torch, n_boxes, md_steps, stream):
+def batch_run(dsea, torch, n_boxes, md_steps, stream, tile=None):
     """Many independent boxes (N log-uniform 500-50,000, rho 0.05-0.9,
-    T 0.7-3.0) advanced together in one graph-captured persistent launch."""
+    T 0.7-3.0) advanced together in one graph-captured persistent launch.
+    tile: a fixed (tile_y, tile_z) for every box instead of the batch
+    autotuner's choice (for profiling, where the autotuner's timings are
+    distorted)."""
     from paper_2507_11289_gb300 import inputs
     specs = inputs.batch_specs(n_boxes=n_boxes, steps=md_steps)
     boxes = []
     try:
         for s in specs:
             pos, vel, box = s.state()
-            boxes.append(dsea.Box(pos, vel, box, precision=dsea.MIXED, stream=stream))
+            kw = dict(tile_y=tile[0], tile_z=tile[1]) if tile else {}
+            boxes.append(dsea.Box(pos, vel, box, precision=dsea.MIXED, stream=stream, **kw))
         bt = dsea.batch_create([b.h for b in boxes])
         n_atoms = sum(b.n_atoms for b in boxes)
         # one unit shape for the whole batch, timed on the batch itself (the
         # boxes fill the GPU together: a lone box's choice is smaller)
         t0 = time.perf_counter()
-        shape = dsea.batch_autotune(bt, trial_steps=3)
+        shape = tuple(tile) if tile else dsea.batch_autotune(bt, trial_steps=3)
         t_tune = time.perf_counter() - t0
         dsea.batch_advance(bt, [10] * len(boxes))          # warm-up, graph capture
         torch.cuda.synchronize()
@@ -487,6 +491,9 @@ def main():
                     help="oracle steps of the all-cores CPU baseline")
     ap.add_argument("--batch-boxes", type=int, default=512)
     ap.add_argument("--batch-md-steps", type=int, default=2000)
+    ap.add_argument("--batch-tile", default="",
+                    help="fixed unit shape 'Y,Z' for every batch box instead of the batch autotuner's "
+                         "(for profiling)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-window", type=float, default=1.0,
                     help="arrival window of the configured stream (s); 60 s would take about half an "
@@ -608,7 +615,8 @@ def main():
                            "unit_shape": [info_b["tile_y"], info_b["tile_z"]],
                            "device_bytes": info_b["device_bytes"]}
     if "batch" not in skip:
-        line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream)
+        tile = tuple(int(x) for x in args.batch_tile.split(",")) if args.batch_tile else None
+        line["batch"] = batch_run(dsea, torch, args.batch_boxes, args.batch_md_steps, stream, tile)
     if "serve" not in skip:
         why = None
         if args.serve_window < 60.0:
