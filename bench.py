@@ -52,8 +52,10 @@ def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
+        import torch
         import torch.distributed as dist
         backend = "nccl"
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))   # each rank's own GPU, before NCCL
         dist.init_process_group(backend=backend)
     return rank, world
 
