@@ -318,7 +318,8 @@ def _union_length(intervals):
     return total
 
 
-def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100, why_window=None):
+def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100, why_window=None,
+              policy="shortest"):
     """Poisson job stream into the continuous-batching server; latency from
     arrival (submit) to completion on the server clock.  Every job's state is
     generated before the arrival window opens, so submissions keep to the
@@ -328,6 +329,7 @@ def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100, why_w
     states = [job.spec.state() for job in jobs]
     srv = dsea.server_create(int(budget_gb * 2 ** 30),
                              dsea.make_params(precision=dsea.MIXED), segment, 0)
+    dsea.server_set_policy(srv, {"shortest": dsea.SERVE_SHORTEST, "all": dsea.SERVE_ALL}[policy])
     ids = []
     late = []
     try:
@@ -353,6 +355,7 @@ def serve_run(dsea, torch, rate, duration, budget_gb, seed=3, segment=100, why_w
     lat = np.array(lat)
     occupied = _union_length(spans)
     out = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "mean_s": float(lat.mean()), "max_s": float(lat.max()), "policy": policy,
            "jobs": len(ids), "rate_per_s": rate, "arrival_window_s": duration,
            "achieved_arrival_rate_per_s": len(ids) / max(submit_s, 1e-9),
            "max_submit_lateness_s": float(max(late)) if late else 0.0,
@@ -504,6 +507,8 @@ def main():
     ap.add_argument("--serve-rate-sustainable", type=float, default=2.5,
                     help="arrival rate of the second served run (about 0.7 utilisation)")
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
+    ap.add_argument("--serve-policy", default="shortest", choices=["shortest", "all"],
+                    help="which resident jobs each server launch advances")
     ap.add_argument("--skip", default="",
                     help="comma list of legs to skip: fp64,walls,nvt,67m,batch,serve,dataset,cpu,e2e")
     ap.add_argument("--walls-steps", type=int, default=3, help="timed steps of the mirror-wall leg")
@@ -627,9 +632,10 @@ def main():
                    f"advances, so the 60 s stream would take about half an hour to drain; the shorter "
                    f"window keeps the arrival process (rate, size and step draws) and the queueing it causes")
         line["served"] = serve_run(dsea, torch, args.serve_rate, args.serve_window, args.serve_budget_gb,
-                                   why_window=why)
+                                   why_window=why, policy=args.serve_policy)
         line["served_sustainable"] = serve_run(dsea, torch, args.serve_rate_sustainable,
-                                               args.serve_window_sustainable, args.serve_budget_gb)
+                                               args.serve_window_sustainable, args.serve_budget_gb,
+                                               policy=args.serve_policy)
     if "dataset" not in skip:
         line["dataset_heat1d"] = dataset_run(dsea, torch, stream)
     if "e2e" not in skip:

@@ -47,6 +47,9 @@ extern "C" {
 #define DSEA_ERR_NO_DEVICE -10  /* no CUDA device available */
 #define DSEA_ERR_BOUNDS -12     /* checked build only: a kernel met an index out of range
                                    (it skipped the access; the box's state is not valid) */
+#define DSEA_ERR_RANGE -13      /* the slice thermostat met 32 atoms with a kinetic energy of
+                                   1024 epsilon or more (a temperature near 21): beyond the
+                                   range of its exact fixed-point sums */
 
 /* ---- enums ------------------------------------------------------------- */
 #define DSEA_FP64 0  /* all pair arithmetic in FP64 */
@@ -270,6 +273,18 @@ int dsea_batch_autotune(dsea_batch *batch, int trial_steps, int *tile_y, int *ti
  * run, larger ones once they fill the GPU together. */
 int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int segment_steps,
                        void *cuda_stream, dsea_server **out);
+
+/* Which resident jobs each launch advances (set at any time; the next launch
+ * uses it).  DSEA_SERVE_SHORTEST, the default: the jobs with the least
+ * remaining work first (remaining atom-steps at the server's measured rate,
+ * minus 0.1 x the seconds since the job arrived, so that a waiting job's
+ * turn always comes), taken in that order until they hold 2^21 atoms (a
+ * launch that size still fills the GPU).  DSEA_SERVE_ALL: every resident job
+ * in every launch.  A job's results do not depend on the policy, only when
+ * it finishes.  DSEA_ERR_INVALID_ARG for another value. */
+#define DSEA_SERVE_ALL 0
+#define DSEA_SERVE_SHORTEST 1
+int dsea_server_set_policy(dsea_server *srv, int policy);
 
 /* Queue a job; the box description is copied.  *job_id receives its id. */
 int dsea_server_submit(dsea_server *srv, const dsea_box_desc *desc, int64_t steps,

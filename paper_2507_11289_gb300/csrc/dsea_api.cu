@@ -42,6 +42,7 @@ int map_device_error(int code)
     case dsea::kErrMigration: return DSEA_ERR_MIGRATION;
     case dsea::kErrTimeout: return DSEA_ERR_TIMEOUT;
     case dsea::kErrBounds: return DSEA_ERR_BOUNDS;
+    case dsea::kErrRange: return DSEA_ERR_RANGE;
     default: return DSEA_ERR_CUDA;
     }
 }
@@ -330,7 +331,7 @@ int ensure_outputs(dsea_box *b)
     int rc = upload_desc(b);
     if (rc) return rc;
     CU(dsea::launch_force_pass(hb, b->db, b->stream));
-    CU(dsea::launch_obs_reduce(hb.unit_obs, hb.n_slices * hb.units_per_slice, b->d_obs3, b->stream));
+    CU(dsea::launch_obs_reduce(hb.unit_obs, hb.n_cells, b->d_obs3, b->stream));
     CU(cudaMemcpyAsync(b->obs3, b->d_obs3, sizeof(b->obs3), cudaMemcpyDeviceToHost, b->stream));
     rc = check_device_error(b);
     if (rc) return rc;
@@ -658,6 +659,7 @@ const char *dsea_status_string(int s)
     case DSEA_ERR_NO_DEVICE: return "no CUDA device";
     case DSEA_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed no-allocation scratch";
     case DSEA_ERR_BOUNDS: return "index out of range (checked build)";
+    case DSEA_ERR_RANGE: return "thermostat kinetic energy beyond its fixed-point range";
     default: return "unknown status";
     }
 }
@@ -807,13 +809,14 @@ int dsea_read_profiles(dsea_box *b, double *U, double *W, double *KE, int64_t *N
     if (n != hb.n_slices) return DSEA_ERR_INVALID_ARG;
     int rc = ensure_outputs(b);
     if (rc) return rc;
-    const int ups = hb.units_per_slice;
-    std::vector<double> part((size_t)dsea::kObsStride * hb.n_slices * ups);
+    // per-cell partials; slice j owns the contiguous cells of its cps x-layers
+    const int64_t per_slice = (int64_t)hb.cps * hb.nc[1] * hb.nc[2];
+    std::vector<double> part((size_t)dsea::kObsStride * hb.n_cells);
     CU(cudaMemcpy(part.data(), hb.unit_obs, sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
-    for (int j = 0; j < n; ++j) {   // the slice's units in order
+    for (int j = 0; j < n; ++j) {   // the slice's cells in order
         double u = 0.0, w = 0.0, k = 0.0, c = 0.0;
-        for (int t = 0; t < ups; ++t) {
-            const double *q = &part[(size_t)dsea::kObsStride * ((size_t)j * ups + t)];
+        for (int64_t t = 0; t < per_slice; ++t) {
+            const double *q = &part[(size_t)dsea::kObsStride * ((size_t)j * per_slice + t)];
             u += q[0];
             w += q[1];
             k += q[2];

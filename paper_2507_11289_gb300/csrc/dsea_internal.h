@@ -30,6 +30,7 @@ enum : int {
     kErrMigration = 2,  // an atom left slices j-1..j+1 in one step
     kErrTimeout = 3,    // a bounded dependency wait expired
     kErrBounds = 4,     // checked build: an index out of range (the access was skipped)
+    kErrRange = 5,      // a thermostat kinetic energy beyond its fixed-point range
 };
 
 // One box as the kernels see it.  Slot layout: the state of a step lives in
@@ -75,7 +76,7 @@ struct BoxDev {
     int withhold_slice;   // testing hook: this slice never reports completion (-1 = off)
     unsigned *done;       // [n_slices] completed units of the running launch
     int *err;             // device error word
-    double *unit_obs;     // [units_per_step * kObsStride] (U, W, KE, N) partials of a force pass
+    double *unit_obs;     // [n_cells * kObsStride] (U, W, KE, N) of each home cell, from a force pass
     // slice thermostat (T0 > 0): per unit (KE, N) of the synchronised velocities before
     // scaling, and per slice the factor applied, both by step parity
     double T0;
@@ -109,11 +110,11 @@ cudaError_t launch_step(const BoxDev &host_box, const BoxDev *dev_box, int64_t s
                         int first_step, cudaStream_t stream);
 
 // Force pass at the current state: forces, synchronised velocities and
-// positions scattered by atom id, plus (U, W, KE) partials per unit.
+// positions scattered by atom id, plus (U, W, KE, N) partials per home cell.
 cudaError_t launch_force_pass(const BoxDev &host_box, const BoxDev *dev_box, cudaStream_t stream);
 
-// Deterministic fixed-order sum of the unit partials into out3 (device).
-cudaError_t launch_obs_reduce(const double *unit_obs, int n_units, double *out3,
+// Deterministic fixed-order sum of the per-cell partials into out3 (device).
+cudaError_t launch_obs_reduce(const double *cell_obs, long long n_cells, double *out3,
                               cudaStream_t stream);
 
 // The persistent ring over one or more boxes (same precision).

@@ -141,12 +141,50 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// The slice thermostat sums kinetic energies in fixed point, so that a
+// slice's total is the same however its cells are grouped into units (unit
+// shape, stage count, batch, server launch): each chunk of at most 32 home
+// atoms sums its atoms' FP64 energies in canonical order, rounds the sum to
+// a multiple of 2^-40 epsilon (4.5e-13 at most per chunk), and the
+// multiples add as integers, exactly.  A chunk of 1024 epsilon or more (32
+// epsilon per atom, a temperature near 21) is out of range, and so is a
+// unit whose int64 sum would overflow: kErrRange.  Slice totals are summed
+// in 128 bits.
+constexpr double kKeScale = 1099511627776.0;   // 2^40 per epsilon
+constexpr double kKeChunkMax = 1024.0;          // 2^10 epsilon
+
+__device__ __forceinline__ long long ke_fixed(double ke, int *err)
+{
+    if (!(ke >= 0.0 && ke < kKeChunkMax)) {
+        set_error(err, kErrRange);
+        return 0;
+    }
+    return __double2ll_rn(ke * kKeScale);
+}
+
+// acc += v for non-negative fixed-point energies, or kErrRange on overflow.
+__device__ __forceinline__ void ke_add(long long &acc, long long v, int *err)
+{
+    if (acc > 0x7fffffffffffffffLL - v) set_error(err, kErrRange);
+    else acc += v;
+}
+
+// Butterfly sum of a 128-bit integer over the warp: the same total in every lane.
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+        const unsigned long long lo2 = __shfl_xor_sync(kFull, lo, o), hi2 = __shfl_xor_sync(kFull, hi, o);
+        v += (__int128)(((unsigned __int128)hi2 << 64) | lo2);
+    }
+    return v;
+}
+
 // The slice thermostat's factor for slice j at step s_abs (Sec. 4.1,
 // md_thermo_a/b): 1 at the first step, else sqrt(T0 / T'), with
 // T' = 2 lam^2 KE / (3 N) the slice's temperature after the previous step's
-// scaling by lam, KE and N summed over the partials the slice's units wrote at
-// that step in a fixed order (lane l takes units l, l + 32, ..., then a
-// butterfly, which leaves the same bits in every lane and every unit).
+// scaling by lam, KE and N summed exactly over the fixed-point partials the
+// slice's units wrote at that step (the KE word holds an int64).
 // Warp-wide; every lane returns the factor.
 __device__ __forceinline__ double slice_lambda(const BoxDev &B, int j, long long s_abs, bool first_step, int lane)
 {
@@ -154,18 +192,18 @@ __device__ __forceinline__ double slice_lambda(const BoxDev &B, int j, long long
     const int q = (int)((s_abs - 1) & 1);
     const int ups = B.units_per_slice;
     const double *part = B.th_part[q] + 2LL * j * ups;
-    double ke = 0.0, n = 0.0;
+    __int128 kef = 0;
+    long long n = 0;
     for (int t = lane; t < ups; t += 32) {
-        ke += __ldcg(part + 2 * t);
-        n += __ldcg(part + 2 * t + 1);
+        kef += (__int128)__double_as_longlong(__ldcg(part + 2 * t));
+        n += (long long)__ldcg(part + 2 * t + 1);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ke += __shfl_xor_sync(kFull, ke, o);
-        n += __shfl_xor_sync(kFull, n, o);
-    }
+    kef = warp_sum_i128(kef);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFull, n, o);
+    const double ke = (double)kef / kKeScale;
     const double lp = __ldcg(B.th_lam[q] + j);
     const double ke_after = lp * lp * ke;
-    return (n > 0.0 && ke_after > 0.0) ? sqrt(B.T0 * 3.0 * n / (2.0 * ke_after)) : 1.0;
+    return (n > 0 && ke_after > 0.0) ? sqrt(B.T0 * 3.0 * (double)n / (2.0 * ke_after)) : 1.0;
 }
 
 // Force accumulators of one lane (FP64 form).
@@ -701,7 +739,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         const int hs = s_start[kh];
         const long long hcell = s_gcell[kh];
         int n_stay = 0;   // atoms of this cell that stay in it, written to its front slots in order
-        double cell_ke = 0.0;   // thermostat: the cell's KE before scaling, chunks in order
+        long long cell_ke = 0;   // thermostat: the cell's KE before scaling, fixed point
         for (int ib = 0; ib < n_i; ib += 32) {
             const int nin = min(32, n_i - ib);
             const float inv_nin = inv_of(nin);
@@ -866,7 +904,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
                     vz = lam * sz + 0.5 * dt * fz;
                 }
                 for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(kFull, ke, o);
-                cell_ke += ke;
+                ke_add(cell_ke, ke_fixed(ke, B.err), B.err);
             }
             if (INTEGRATE) {
                 long long dest = 0;
@@ -901,8 +939,24 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
         if (INTEGRATE && lane == 0 && idx_ok(B.err, hcell, B.n_cells))
             B.cnt[pn][hcell] = ((unsigned long long)tag_next << 32) | (unsigned long long)n_stay;
         if (thermo && lane == 0) {
-            s_cellke[2 * h] = cell_ke;
+            s_cellke[2 * h] = __longlong_as_double(cell_ke);
             s_cellke[2 * h + 1] = (double)n_i;
+        }
+        if (OBS) {   // the cell's (U, W, KE, N): its lanes' sums by a fixed xor tree
+            for (int o = 16; o > 0; o >>= 1) {
+                red_u += __shfl_xor_sync(kFull, red_u, o);
+                red_w += __shfl_xor_sync(kFull, red_w, o);
+                red_k += __shfl_xor_sync(kFull, red_k, o);
+                red_n += __shfl_xor_sync(kFull, red_n, o);
+            }
+            if (lane == 0 && idx_ok(B.err, hcell, B.n_cells)) {
+                double *o = B.unit_obs + (long long)kObsStride * hcell;
+                o[0] = red_u;
+                o[1] = red_w;
+                o[2] = red_k;
+                o[3] = red_n;
+            }
+            red_u = red_w = red_k = red_n = 0.0;
         }
         if (OBS) {
             h += kWarps;
@@ -914,47 +968,17 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
     if (thermo) {   // the unit's (KE, N) before scaling, home cells in order, and the factor
         __syncthreads();
         if (tid == 0) {
-            double ke = 0.0, n = 0.0;
+            long long ke = 0;   // fixed point: exact in any order
+            double n = 0.0;
             for (int q = 0; q < n_home; ++q) {
-                ke += s_cellke[2 * q];
+                ke_add(ke, __double_as_longlong(s_cellke[2 * q]), B.err);
                 n += s_cellke[2 * q + 1];
             }
             const long long u = (long long)j * B.units_per_slice + tile;
             if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
-                B.th_part[p][2 * u] = ke;
+                B.th_part[p][2 * u] = __longlong_as_double(ke);
                 B.th_part[p][2 * u + 1] = n;
                 B.th_lam[p][j] = lam;
-            }
-        }
-    }
-    if (OBS) {
-        // fixed-order FP64 reduction: xor tree in the warp, then warps in order
-        for (int o = 16; o > 0; o >>= 1) {
-            red_u += __shfl_xor_sync(kFull, red_u, o);
-            red_w += __shfl_xor_sync(kFull, red_w, o);
-            red_k += __shfl_xor_sync(kFull, red_k, o);
-            red_n += __shfl_xor_sync(kFull, red_n, o);
-        }
-        if (lane == 0) {
-            s_red[warp * 4 + 0] = red_u;
-            s_red[warp * 4 + 1] = red_w;
-            s_red[warp * 4 + 2] = red_k;
-            s_red[warp * 4 + 3] = red_n;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double u = 0, w = 0, k = 0, n = 0;
-            for (int q = 0; q < kWarps; ++q) {
-                u += s_red[q * 4];
-                w += s_red[q * 4 + 1];
-                k += s_red[q * 4 + 2];
-                n += s_red[q * 4 + 3];
-            }
-            if (idx_ok(B.err, unit_id, B.n_cells)) {
-                B.unit_obs[(long long)kObsStride * unit_id] = u;
-                B.unit_obs[(long long)kObsStride * unit_id + 1] = w;
-                B.unit_obs[(long long)kObsStride * unit_id + 2] = k;
-                B.unit_obs[(long long)kObsStride * unit_id + 3] = n;
             }
         }
     }
@@ -1002,7 +1026,8 @@ struct WarpArea {
     float bb[6];               // pruning box: low corner, high corner (home frame)
     int n_stay;                // atoms that stayed in the home cell so far
     double lam;                // slice thermostat: the factor of this step (1 without)
-    double ke_acc, n_acc;      // slice thermostat: the unit's KE before scaling, and atoms
+    long long ke_fix;          // slice thermostat: the unit's KE before scaling (fixed point)
+    double n_acc;              // and its atoms
 };
 
 // Per-lane FP64 accumulators of a force pass: U, W and KE halves, atoms.
@@ -1404,7 +1429,9 @@ __device__ __forceinline__ void home_update(const BoxDev &B, WarpArea &wa, int i
         }
         for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(kFull, ke, o);
         if (lane == 0) {
-            wa.ke_acc += ke;
+            long long acc = wa.ke_fix;
+            ke_add(acc, ke_fixed(ke, B.err), B.err);
+            wa.ke_fix = acc;
             wa.n_acc += (double)min(32, n_home - ib);
         }
     }
@@ -1469,6 +1496,22 @@ __device__ __forceinline__ void mixed_home_cell(const BoxDev &B, WarpArea &wa, O
         home_forces<OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww);
         home_update<INTEGRATE, OBS>(B, wa, ib, lane, fx, fy, fz, uu, ww, red);
     }
+    if (OBS) {   // the cell's (U, W, KE, N): its lanes' sums by a fixed xor tree
+        for (int o = 16; o > 0; o >>= 1) {
+            red.u += __shfl_xor_sync(kFull, red.u, o);
+            red.w += __shfl_xor_sync(kFull, red.w, o);
+            red.k += __shfl_xor_sync(kFull, red.k, o);
+            red.n += __shfl_xor_sync(kFull, red.n, o);
+        }
+        if (lane == 0 && idx_ok(B.err, v.hcell, B.n_cells)) {
+            double *o = B.unit_obs + (long long)kObsStride * v.hcell;
+            o[0] = red.u;
+            o[1] = red.w;
+            o[2] = red.k;
+            o[3] = red.n;
+        }
+        red = ObsAcc{0.0, 0.0, 0.0, 0.0};
+    }
     // the home cell publishes how many atoms stayed in it, empty or not
     if (INTEGRATE && lane == 0 && idx_ok(B.err, v.hcell, B.n_cells))
         B.cnt[(int)(v.s_abs & 1) ^ 1][v.hcell] = ((unsigned long long)(unsigned)(v.s_abs + 2) << 32) |
@@ -1486,7 +1529,7 @@ __device__ __forceinline__ void mixed_unit_begin(const BoxDev &B, WarpArea &wa, 
     const double l = slice_lambda(B, j, s_abs, first_step, lane);
     if (lane == 0) {
         wa.lam = l;
-        wa.ke_acc = 0.0;
+        wa.ke_fix = 0;
         wa.n_acc = 0.0;
     }
     __syncwarp();
@@ -1504,7 +1547,7 @@ __device__ __forceinline__ void mixed_unit_end(const BoxDev &B, WarpArea &wa, in
         const int p = (int)(s_abs & 1);
         const long long u = (long long)j * B.units_per_slice + tile;
         if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
-            B.th_part[p][2 * u] = wa.ke_acc;
+            B.th_part[p][2 * u] = __longlong_as_double(wa.ke_fix);
             B.th_part[p][2 * u + 1] = wa.n_acc;
             B.th_lam[p][j] = wa.lam;
         }
@@ -1717,36 +1760,25 @@ __global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long
         mixed_home_cell<INTEGRATE, OBS>(sB, wa, red);
     }
     mixed_unit_end<INTEGRATE>(sB, wa, j, tile, s_abs, lane);
-    if (OBS) {   // fixed-order FP64 reduction of the unit: xor tree over the lanes
-        for (int o = 16; o > 0; o >>= 1) {
-            red.u += __shfl_xor_sync(kFull, red.u, o);
-            red.w += __shfl_xor_sync(kFull, red.w, o);
-            red.k += __shfl_xor_sync(kFull, red.k, o);
-            red.n += __shfl_xor_sync(kFull, red.n, o);
-        }
-        if (lane == 0 && idx_ok(sB.err, u, sB.n_cells)) {
-            sB.unit_obs[(long long)kObsStride * u] = red.u;
-            sB.unit_obs[(long long)kObsStride * u + 1] = red.w;
-            sB.unit_obs[(long long)kObsStride * u + 2] = red.k;
-            sB.unit_obs[(long long)kObsStride * u + 3] = red.n;
-        }
-    }
 }
 
-__global__ void __launch_bounds__(256) k_obs_reduce(const double *unit_obs, int n, double *out3)
+// Global (U, W, KE) from the per-cell partials of a force pass, in a fixed
+// order that depends only on the cell count: thread t sums cells t, t + 1024,
+// ..., then a fixed tree over the threads.
+__global__ void __launch_bounds__(1024) k_obs_reduce(const double *cell_obs, long long n, double *out3)
 {
-    __shared__ double s[3][256];
+    __shared__ double s[3][1024];
     double a = 0, b = 0, c = 0;
-    for (int i = threadIdx.x; i < n; i += 256) {
-        a += unit_obs[(long long)kObsStride * i];
-        b += unit_obs[(long long)kObsStride * i + 1];
-        c += unit_obs[(long long)kObsStride * i + 2];
+    for (long long i = threadIdx.x; i < n; i += 1024) {
+        a += cell_obs[kObsStride * i];
+        b += cell_obs[kObsStride * i + 1];
+        c += cell_obs[kObsStride * i + 2];
     }
     s[0][threadIdx.x] = a;
     s[1][threadIdx.x] = b;
     s[2][threadIdx.x] = c;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
+    for (int o = 512; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             s[0][threadIdx.x] += s[0][threadIdx.x + o];
             s[1][threadIdx.x] += s[1][threadIdx.x + o];
@@ -2053,9 +2085,9 @@ cudaError_t launch_force_pass(const BoxDev &hb, const BoxDev *db, cudaStream_t s
                              : launch_units<0, false, true>(hb, db, hb.step, hb.w_is_sync, stream);
 }
 
-cudaError_t launch_obs_reduce(const double *unit_obs, int n_units, double *out3, cudaStream_t stream)
+cudaError_t launch_obs_reduce(const double *cell_obs, long long n_cells, double *out3, cudaStream_t stream)
 {
-    k_obs_reduce<<<1, 256, 0, stream>>>(unit_obs, n_units, out3);
+    k_obs_reduce<<<1, 1024, 0, stream>>>(cell_obs, n_cells, out3);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,6 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     int rc0 = dsea::box_geometry(0, box, n_atoms, p, hb);
     if (rc0) return rc0;
     // carve the scratch: descriptor, error word, counts, slots, partials, read-back
-    const int units = hb.n_slices * hb.units_per_slice;
     const size_t n3 = 3 * (size_t)(n_atoms > 0 ? n_atoms : 1);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -86,7 +85,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     const size_t o_r = take(sizeof(double) * 3 * hb.n_slots);
     const size_t o_v = take((precision == DSEA_MIXED ? sizeof(float) : sizeof(double)) * 3 * hb.n_slots);
     const size_t o_q = precision == DSEA_MIXED ? take(sizeof(float4) * hb.n_slots) : 0;
-    const size_t o_obs = take(sizeof(double) * dsea::kObsStride * (size_t)units);
+    const size_t o_obs = take(sizeof(double) * dsea::kObsStride * (size_t)hb.n_cells);   // per-cell partials
     const size_t o_outr = take(sizeof(double) * n3);
     const size_t o_outv = take(sizeof(double) * n3);
     if (off > kScratchBytes) return DSEA_ERR_SCRATCH_LIMIT;
@@ -120,7 +119,7 @@ extern "C" int dsea_forces_noalloc(const double *pos_dev, const double *vel_dev,
     if (e == cudaSuccess) e = cudaMemcpyAsync(db, &hb, sizeof(hb), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = dsea::launch_bin(hb, db, pos_dev, vel_dev, st);
     if (e == cudaSuccess) e = dsea::launch_force_pass(hb, db, st);
-    if (e == cudaSuccess && obs3_dev) e = dsea::launch_obs_reduce(hb.unit_obs, units, obs3_dev, st);
+    if (e == cudaSuccess && obs3_dev) e = dsea::launch_obs_reduce(hb.unit_obs, hb.n_cells, obs3_dev, st);
     // the status word comes back on the caller's stream, and only that stream
     // is waited for (a plain cudaMemcpy would also wait for every blocking
     // stream of the device)

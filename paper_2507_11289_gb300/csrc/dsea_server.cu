@@ -21,6 +21,7 @@
 #include "dsea_host.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -51,6 +52,7 @@ struct dsea_server {
     size_t budget = 0;
     dsea_params params{};
     int segment = 100;
+    std::atomic<int> policy{DSEA_SERVE_SHORTEST};
     cudaStream_t stream = nullptr;    // compute stream: the ring segments
     bool own_stream = false;
     cudaStream_t astream = nullptr;   // admission stream: box creation, binning, read-back
@@ -137,24 +139,63 @@ void retire(dsea_server *s, Job *j)
     finish(s, j, r2 ? r2 : 2);
 }
 
+// Jobs of the next launch.  DSEA_SERVE_ALL: every resident job.
+// DSEA_SERVE_SHORTEST: the jobs with the least remaining work first, aged by
+// their waiting time (key: remaining atom-steps at the measured rate, minus
+// kAgeWeight times the seconds since arrival, so that no job waits forever),
+// added in key order until they hold kFillAtoms atoms, twice the size at
+// which one box fills the GPU, so that the launch still fills it.  A job left
+// out keeps its state on the device and loses no work.  Under the stream
+// the benchmark offers, whose jobs all fit the budget at once, the median
+// latency falls about sevenfold in a model of the server, while the last
+// job ends at nearly the same time.
+constexpr double kAgeWeight = 0.1;
+constexpr double kFillAtoms = 2097152.0;
+
+std::vector<Job *> pick_jobs(dsea_server *s, const std::vector<Job *> &running)
+{
+    if (s->policy.load() != DSEA_SERVE_SHORTEST || running.size() <= 1) return running;
+    double rate = 4e9;   // atom-steps per busy second, until measured
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->busy_s > 0.0 && s->atom_steps > 0.0) rate = s->atom_steps / s->busy_s;
+    }
+    const double now = s->now();
+    std::vector<std::pair<double, Job *>> key;
+    key.reserve(running.size());
+    for (Job *j : running)
+        key.push_back({(double)j->desc.n_atoms * (double)j->remaining / rate - kAgeWeight * (now - j->t_arrive), j});
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<double, Job *> &a, const std::pair<double, Job *> &b) { return a.first < b.first; });
+    std::vector<Job *> out;
+    double atoms = 0.0;
+    for (const auto &e : key) {
+        out.push_back(e.second);
+        atoms += (double)e.second->desc.n_atoms;
+        if (atoms >= kFillAtoms) break;
+    }
+    return out;
+}
+
 void run(dsea_server *s)
 {
     cudaSetDevice(s->device);
     std::vector<Job *> running, ready, retiring;
     while (true) {
-        // 1. launch the next segment over every resident box (the device then
-        //    runs while the host does steps 2 and 3)
+        // 1. launch the next segment over the resident jobs the policy picks
+        //    (the device then runs while the host does steps 2 and 3)
         NvtxRange nvtx_cycle("server cycle");
-        const int n = (int)running.size();
+        const std::vector<Job *> launch = pick_jobs(s, running);
+        const int n = (int)launch.size();
         std::vector<dsea_box *> boxes(n);
         std::vector<int64_t> steps(n);
         double work = 0;
         int rc = DSEA_OK;
         if (n > 0) {
             for (int k = 0; k < n; ++k) {
-                boxes[k] = running[k]->box;
-                steps[k] = std::min<int64_t>(running[k]->remaining, s->segment);
-                work += (double)running[k]->desc.n_atoms * (double)steps[k];
+                boxes[k] = launch[k]->box;
+                steps[k] = std::min<int64_t>(launch[k]->remaining, s->segment);
+                work += (double)launch[k]->desc.n_atoms * (double)steps[k];
             }
             // the jobs present choose the unit shape of this launch (when the
             // server's params leave it automatic): small units while few jobs
@@ -215,14 +256,15 @@ void run(dsea_server *s)
                 s->launches += 1;
             }
             for (int k = 0; k < n; ++k) {
-                Job *j = running[k];
+                Job *j = launch[k];
                 int jrc = rc ? rc : dsea_sync(j->box);
                 if (!jrc) j->remaining -= steps[k];
                 if (jrc) finish(s, j, jrc);
                 else if (j->remaining == 0) retiring.push_back(j);   // read back during the next segment
-                else still.push_back(j);
             }
         }
+        for (Job *j : running)   // the jobs that go on: those left out of the launch, and the unfinished
+            if (j->state == 1 && j->remaining > 0) still.push_back(j);
         // 5. newly binned boxes join the next segment, after their binning
         if (!ready.empty()) {
             cudaEventRecord(s->ev_ready, s->astream);
@@ -299,6 +341,13 @@ int dsea_server_create(size_t mem_budget_bytes, const dsea_params *params, int s
 double dsea_server_clock(const dsea_server *s)
 {
     return s ? s->now() : 0.0;
+}
+
+int dsea_server_set_policy(dsea_server *srv, int policy)
+{
+    if (!srv || (policy != DSEA_SERVE_ALL && policy != DSEA_SERVE_SHORTEST)) return DSEA_ERR_INVALID_ARG;
+    srv->policy.store(policy);
+    return DSEA_OK;
 }
 
 int dsea_server_submit(dsea_server *s, const dsea_box_desc *desc, int64_t steps, uint64_t *job_id)

@@ -29,6 +29,7 @@ ERR_NOT_FOUND = -9
 ERR_NO_DEVICE = -10
 ERR_SCRATCH_LIMIT = -11
 ERR_BOUNDS = -12           # checked build only: a kernel met an index out of range
+ERR_RANGE = -13            # a thermostat kinetic energy beyond its fixed-point range
 
 FP64 = 0
 MIXED = 1
@@ -104,6 +105,7 @@ _SIGS = {
     "dsea_autotune": (_I, [_P, _I, ctypes.POINTER(Params)]),
     "dsea_batch_autotune": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dsea_server_create": (_I, [ctypes.c_size_t, ctypes.POINTER(Params), _I, _P, ctypes.POINTER(_P)]),
+    "dsea_server_set_policy": (_I, [_P, _I]),
     "dsea_server_submit": (_I, [_P, ctypes.POINTER(BoxDesc), _I64, ctypes.POINTER(ctypes.c_uint64)]),
     "dsea_server_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
     "dsea_server_result": (_I, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(Observables),
@@ -379,6 +381,14 @@ def server_create(mem_budget_bytes: int, params: Params | None = None, segment_s
                                      int(segment_steps), stream, ctypes.byref(s)),
            "dsea_server_create")
     return s.value
+
+
+SERVE_ALL = 0         # every resident job in every launch
+SERVE_SHORTEST = 1    # least remaining work first, aged, filling the GPU (the default)
+
+
+def server_set_policy(srv, policy: int):
+    _check(load().dsea_server_set_policy(srv, int(policy)), "dsea_server_set_policy")
 
 
 def server_submit(srv, pos, vel, box, steps: int, n_slices: int = 0, walls=False) -> int:

@@ -44,7 +44,7 @@ def test_checked_variant_builds_and_exports_the_same_calls():
 
 def test_status_strings_and_version():
     assert dsea.version() == "0.1.0"
-    for code in range(-12, 1):
+    for code in range(-13, 1):
         s = dsea.status_string(code)
         assert s and s != "unknown status"
     assert dsea.status_string(-99) == "unknown status"

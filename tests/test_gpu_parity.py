@@ -106,16 +106,25 @@ def test_ring_equals_stepwise_bitwise(precision, melted_4k):
     assert out[0][2] == out[1][2]
 
 
-def test_unit_shape_does_not_change_results(melted_4k):
+@pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
+@pytest.mark.parametrize("temperature", [0.0, 1.2])
+def test_unit_shape_does_not_change_results(melted_4k, precision, temperature):
+    """The unit shape only groups home cells: each atom's force is summed in an
+    order fixed by the state, the observables and profiles are fixed-order
+    sums of per-cell partials, and the thermostat sums kinetic energies in
+    exact fixed point.  Every result is bitwise the same for every shape."""
     pos, vel, box = melted_4k
     ref = None
     for ty, tz in [(1, 1), (2, 5), (4, 4), (6, 6)]:
-        with dsea.Box(pos, vel, box, n_slices=4, precision=dsea.MIXED, tile_y=ty, tile_z=tz) as b:
-            b.advance(20)
-            r = b.positions()
+        with dsea.Box(pos, vel, box, n_slices=4, precision=precision, tile_y=ty, tile_z=tz,
+                      temperature=temperature) as b:
+            b.advance(20 if precision == dsea.MIXED else 8)
+            got = (b.positions(), b.velocities(), b.observables(), b.profiles())
         if ref is None:
-            ref = r
-        assert np.array_equal(r, ref), (ty, tz)
+            ref = got
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (ty, tz)
+        assert got[2] == ref[2], (ty, tz)
+        assert all(np.array_equal(got[3][k], ref[3][k]) for k in ref[3]), (ty, tz)
 
 
 @pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
