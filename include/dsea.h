@@ -200,7 +200,10 @@ int dsea_read_positions(dsea_box *box, double *out_xyz, int64_t n);
 int dsea_read_velocities(dsea_box *box, double *out_xyz, int64_t n);
 int dsea_read_forces(dsea_box *box, double *out_xyz, int64_t n);
 
-/* Observables at the current step (Algorithm 1's U and V, and KE). */
+/* Observables at the current step (Algorithm 1's U and V, and KE): FP64
+ * sums of per-cell partials (each cell's atoms in canonical order) over the
+ * cells in a fixed order, so the same bits whatever the unit shape, stage
+ * count, batch or server launch the box ran in. */
 int dsea_read_observables(dsea_box *box, dsea_observables *out);
 
 /* Spatially resolved observables at the current step (Sec. 4.2: per-slice
