@@ -107,3 +107,24 @@ def test_caller_arrays_may_change_after_create():
     finally:
         dsea.box_destroy(h)
         dsea.box_destroy(h0)
+
+
+@pytest.mark.parametrize("precision", [dsea.MIXED, dsea.FP64])
+def test_thermostat_energy_beyond_its_range_is_reported(precision):
+    """The slice thermostat sums kinetic energies exactly in fixed point; a
+    chunk of home atoms at 1024 epsilon or more is outside that range and is
+    reported as DSEA_ERR_RANGE (here one atom at 50 sigma/tau, 1250 epsilon,
+    alone in its cell).  The same state without the thermostat runs."""
+    from tests.test_oracle_nvt import _gas
+    pos, vel, box, _, _ = _gas(60, [1.0, 1.0, 1.0])
+    vel = vel.copy()
+    vel[0] = [50.0, 0.0, 0.0]
+    with dsea.Box(pos, vel, box, n_slices=3, precision=precision, temperature=1.0) as b:
+        b.advance(2)
+        with pytest.raises(dsea.DseaError) as e:
+            b.sync()
+        assert e.value.code == dsea.ERR_RANGE
+    with dsea.Box(pos, vel, box, n_slices=3, precision=precision) as b:
+        b.advance(2)
+        b.sync()
+    _still_usable()
