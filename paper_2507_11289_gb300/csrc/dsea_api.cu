@@ -261,7 +261,7 @@ int ring_launch_single(dsea_box *b, int64_t n)
     CU(cudaMemcpyAsync(b->d_cum, cum, sizeof(cum), cudaMemcpyHostToDevice, b->stream));
     int rc = upload_desc(b);
     if (rc) return rc;
-    CU(cudaMemsetAsync(hb.done, 0, sizeof(unsigned) * hb.n_slices, b->stream));
+    CU(cudaMemsetAsync(hb.done, 0, sizeof(unsigned) * 2 * hb.n_slices, b->stream));
     CU(cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned long long), b->stream));
     CU(cudaMemsetAsync(b->d_launch_err, 0, sizeof(int), b->stream));
     dsea::RingPlan plan{};
@@ -293,6 +293,8 @@ int advance_impl(dsea_box *b, int64_t n)
     if (rc) return rc;
     if (b->params.schedule == DSEA_SCHED_STEPWISE) {
         for (int64_t s = 0; s < n; ++s) {
+            if (hb.T0 > 0.0)   // the thermostat's per-slice unit counts restart every step
+                CU(cudaMemsetAsync(hb.done + hb.n_slices, 0, sizeof(unsigned) * hb.n_slices, b->stream));
             CU(dsea::launch_step(hb, b->db, hb.step + s, (hb.w_is_sync && s == 0) ? 1 : 0, b->stream));
         }
         hb.step += n;
@@ -582,7 +584,7 @@ int register_impl(dsea_box *b, const dsea_params *params)
     // device state
     b->db = (BoxDev *)dev_alloc(b, sizeof(BoxDev));
     hb.err = (int *)dev_alloc(b, sizeof(int));
-    hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * n_s);
+    hb.done = (unsigned *)dev_alloc(b, sizeof(unsigned) * 2 * n_s);   // completion, thermostat counts
     const int64_t max_units = hb.n_cells;   // any tile shape has at most one unit per cell
     hb.unit_obs = (double *)dev_alloc(b, sizeof(double) * dsea::kObsStride * (size_t)max_units);
     hb.T0 = p.temperature;
@@ -1313,7 +1315,7 @@ int multi_enqueue(MultiPlan &mp, dsea_box *const *boxes, cudaStream_t st)
                        cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(mp.d_active, mp.h_active, sizeof(int) * mp.smax, cudaMemcpyHostToDevice, st));
     for (int k = 0; k < n; ++k)
-        CU(cudaMemsetAsync(boxes[k]->hb.done, 0, sizeof(unsigned) * boxes[k]->hb.n_slices, st));
+        CU(cudaMemsetAsync(boxes[k]->hb.done, 0, sizeof(unsigned) * 2 * boxes[k]->hb.n_slices, st));
     CU(cudaMemsetAsync(mp.d_ticket, 0, sizeof(unsigned long long), st));
     CU(cudaMemsetAsync(mp.d_err, 0, sizeof(int), st));
     RingPlan plan{};

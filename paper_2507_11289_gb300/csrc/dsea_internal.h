@@ -74,7 +74,8 @@ struct BoxDev {
     int64_t step;   // absolute step of the current state
     int w_is_sync;  // 1 until the first step: v holds v(t0), not v(t-dt/2)
     int withhold_slice;   // testing hook: this slice never reports completion (-1 = off)
-    unsigned *done;       // [n_slices] completed units of the running launch
+    unsigned *done;       // [n_slices] completed units of the running launch, then
+                          // [n_slices] units whose thermostat partial is written
     int *err;             // device error word
     double *unit_obs;     // [n_cells * kObsStride] (U, W, KE, N) of each home cell, from a force pass
     // slice thermostat (T0 > 0): per unit (KE, N) of the synchronised velocities before

@@ -180,30 +180,72 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
     return v;
 }
 
-// The slice thermostat's factor for slice j at step s_abs (Sec. 4.1,
-// md_thermo_a/b): 1 at the first step, else sqrt(T0 / T'), with
-// T' = 2 lam^2 KE / (3 N) the slice's temperature after the previous step's
-// scaling by lam, KE and N summed exactly over the fixed-point partials the
-// slice's units wrote at that step (the KE word holds an int64).
-// Warp-wide; every lane returns the factor.
-__device__ __forceinline__ double slice_lambda(const BoxDev &B, int j, long long s_abs, bool first_step, int lane)
+// The slice thermostat's factor for slice j at step s_abs + 1 (Sec. 4.1,
+// md_thermo_a/b): sqrt(T0 / T'), with T' = 2 lp^2 KE / (3 N) the slice's
+// temperature after step s_abs's scaling by lp, KE and N summed exactly over
+// the fixed-point partials the slice's units wrote at step s_abs (the KE
+// word holds an int64).  Warp-wide; every lane returns the factor.
+__device__ __forceinline__ double slice_lambda_next(const BoxDev &B, int j, long long s_abs, double lp, int lane)
 {
-    if (first_step) return 1.0;
-    const int q = (int)((s_abs - 1) & 1);
+    const int q = (int)(s_abs & 1);
     const int ups = B.units_per_slice;
     const double *part = B.th_part[q] + 2LL * j * ups;
     __int128 kef = 0;
     long long n = 0;
-    for (int t = lane; t < ups; t += 32) {
-        kef += (__int128)__double_as_longlong(__ldcg(part + 2 * t));
-        n += (long long)__ldcg(part + 2 * t + 1);
+    // eight partials per lane in flight at once: one L2 round trip, not eight
+    for (int t0 = lane; t0 < ups; t0 += 32 * 8) {
+        double kv[8], nv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int t = t0 + 32 * k;
+            kv[k] = t < ups ? __ldcg(part + 2 * t) : 0.0;
+            nv[k] = t < ups ? __ldcg(part + 2 * t + 1) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            kef += (__int128)__double_as_longlong(kv[k]);
+            n += (long long)nv[k];
+        }
     }
     kef = warp_sum_i128(kef);
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFull, n, o);
     const double ke = (double)kef / kKeScale;
-    const double lp = __ldcg(B.th_lam[q] + j);
     const double ke_after = lp * lp * ke;
     return (n > 0 && ke_after > 0.0) ? sqrt(B.T0 * 3.0 * (double)n / (2.0 * ke_after)) : 1.0;
+}
+
+// The factor of slice j at step s_abs: 1 at the first step, else the value
+// the slice's last unit of the previous step published (slice_publish).
+__device__ __forceinline__ double slice_factor(const BoxDev &B, int j, long long s_abs, bool first_step)
+{
+    return first_step ? 1.0 : __ldcg(B.th_lam[(int)(s_abs & 1)] + j);
+}
+
+// After a unit of slice j at relative level s_rel of this launch (step
+// s_abs, factor lam) wrote its partial: count it on the slice's counter
+// (after the per-slice completion counters in `done`); the level's last unit
+// computes the factor of step s_abs + 1 from all the partials and publishes
+// it before its own completion is counted, so the next level's units, which
+// wait for that completion, find it.  One computation per slice and step
+// instead of one per unit.  Warp-wide.
+__device__ __forceinline__ void slice_publish(const BoxDev &B, int j, long long s_abs, int s_rel, double lam,
+                                              int lane)
+{
+    unsigned last = 0;
+    if (lane == 0 && idx_ok(B.err, j, B.n_slices)) {
+        __threadfence();   // this unit's partial before the count
+        const unsigned want = (unsigned)B.units_per_slice * (unsigned)(s_rel + 1);
+        last = atomicAdd(B.done + B.n_slices + j, 1u) + 1u == want ? 1u : 0u;
+    }
+    last = __shfl_sync(kFull, last, 0);
+    if (!last) return;
+    __threadfence();   // the other units' partials, counted before this one
+    const double l = slice_lambda_next(B, j, s_abs, lam, lane);
+    if (lane == 0) {
+        B.th_lam[(int)((s_abs + 1) & 1)][j] = l;
+        __threadfence();
+    }
+    __syncwarp();
 }
 
 // Force accumulators of one lane (FP64 form).
@@ -538,7 +580,7 @@ __device__ __forceinline__ int move_axis(double &r, float q, float d, int cg, do
 // s_abs: absolute step of the input state.
 template <bool INTEGRATE, bool OBS>
 __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, bool first_step,
-                             int unit_id, char *smem)
+                             int s_rel, char *smem)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = (int)(s_abs & 1);
@@ -711,10 +753,7 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             }
         }
     }
-    if (thermo && warp == 0) {   // the slice thermostat's factor of this step
-        const double l = slice_lambda(B, j, s_abs, first_step, lane);
-        if (lane == 0) *s_lam = l;
-    }
+    if (thermo && tid == 0) *s_lam = slice_factor(B, j, s_abs, first_step);   // this step's factor
     __syncthreads();
 
     // 4./5. forces, then kick, drift and rebin, warp per home cell.  Without
@@ -965,21 +1004,24 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
             h = __shfl_sync(kFull, h, 0);
         }
     }
-    if (thermo) {   // the unit's (KE, N) before scaling, home cells in order, and the factor
+    if (thermo) {   // the unit's (KE, N) before scaling, home cells in order; the next factor
         __syncthreads();
-        if (tid == 0) {
-            long long ke = 0;   // fixed point: exact in any order
-            double n = 0.0;
-            for (int q = 0; q < n_home; ++q) {
-                ke_add(ke, __double_as_longlong(s_cellke[2 * q]), B.err);
-                n += s_cellke[2 * q + 1];
+        if (warp == 0) {
+            if (lane == 0) {
+                long long ke = 0;   // fixed point: exact in any order
+                double n = 0.0;
+                for (int q = 0; q < n_home; ++q) {
+                    ke_add(ke, __double_as_longlong(s_cellke[2 * q]), B.err);
+                    n += s_cellke[2 * q + 1];
+                }
+                const long long u = (long long)j * B.units_per_slice + tile;
+                if (idx_ok(B.err, u, B.n_cells)) {   // n_cells: units allocated
+                    B.th_part[p][2 * u] = __longlong_as_double(ke);
+                    B.th_part[p][2 * u + 1] = n;
+                }
             }
-            const long long u = (long long)j * B.units_per_slice + tile;
-            if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
-                B.th_part[p][2 * u] = __longlong_as_double(ke);
-                B.th_part[p][2 * u + 1] = n;
-                B.th_lam[p][j] = lam;
-            }
+            __syncwarp();
+            slice_publish(B, j, s_abs, s_rel, lam, lane);
         }
     }
 }
@@ -1526,9 +1568,8 @@ __device__ __forceinline__ void mixed_unit_begin(const BoxDev &B, WarpArea &wa, 
                                                  bool first_step, int lane)
 {
     if (!INTEGRATE || !(B.T0 > 0.0)) return;
-    const double l = slice_lambda(B, j, s_abs, first_step, lane);
     if (lane == 0) {
-        wa.lam = l;
+        wa.lam = slice_factor(B, j, s_abs, first_step);
         wa.ke_fix = 0;
         wa.n_acc = 0.0;
     }
@@ -1539,19 +1580,21 @@ __device__ __forceinline__ void mixed_unit_begin(const BoxDev &B, WarpArea &wa, 
 // the slice's units of the next step.
 template <bool INTEGRATE>
 __device__ __forceinline__ void mixed_unit_end(const BoxDev &B, WarpArea &wa, int j, int tile, long long s_abs,
-                                               int lane)
+                                               int s_rel, int lane)
 {
     if (!INTEGRATE || !(B.T0 > 0.0)) return;
     __syncwarp();
     if (lane == 0) {
         const int p = (int)(s_abs & 1);
         const long long u = (long long)j * B.units_per_slice + tile;
-        if (idx_ok(B.err, u, B.n_cells) && idx_ok(B.err, j, B.n_slices)) {   // n_cells: units allocated
+        if (idx_ok(B.err, u, B.n_cells)) {   // n_cells: units allocated
             B.th_part[p][2 * u] = __longlong_as_double(wa.ke_fix);
             B.th_part[p][2 * u + 1] = wa.n_acc;
-            B.th_lam[p][j] = wa.lam;
         }
     }
+    __syncwarp();
+    const volatile WarpArea &v = wa;
+    slice_publish(B, j, s_abs, s_rel, v.lam, lane);
 }
 
 // Home cell h of unit (j, tile) (z fastest, then y, then x) into wa.hx/hy/hz.
@@ -1730,7 +1773,7 @@ __global__ void __launch_bounds__(kThreads) k_units_f64(const BoxDev *bp, long l
     __syncthreads();
     const int u = blockIdx.x;
     const int j = u / sB.units_per_slice, tile = u - j * sB.units_per_slice;
-    run_unit_f64<INTEGRATE, OBS>(sB, j, tile, s_abs, first != 0, u, smem);
+    run_unit_f64<INTEGRATE, OBS>(sB, j, tile, s_abs, first != 0, 0, smem);   // one step per launch
 }
 
 // Mixed form, one step or force pass: one warp per unit (warp w of block b
@@ -1759,7 +1802,7 @@ __global__ void __launch_bounds__(kThreads) k_units_mixed(const BoxDev *bp, long
         set_unit_cell(sB, wa, j, tile, h);
         mixed_home_cell<INTEGRATE, OBS>(sB, wa, red);
     }
-    mixed_unit_end<INTEGRATE>(sB, wa, j, tile, s_abs, lane);
+    mixed_unit_end<INTEGRATE>(sB, wa, j, tile, s_abs, 0, lane);   // one step per launch
 }
 
 // Global (U, W, KE) from the per-cell partials of a force pass, in a fixed
@@ -1882,7 +1925,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(Rin
         const int s_rel = s_dec[0], j = s_dec[1], tile = s_dec[2];
         const long long s_abs = sB.step + s_rel;
         if (s_go == 1)
-            run_unit_f64<true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, 0, smem);
+            run_unit_f64<true, false>(sB, j, tile, s_abs, s_rel == 0 && sB.w_is_sync, s_rel, smem);
         __threadfence();
         __syncthreads();
         if (tid == 0 && !(j == sB.withhold_slice && s_rel == 0) && idx_ok(sB.err, j, sB.n_slices))
@@ -1986,7 +2029,7 @@ __global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_mixed(R
                 set_unit_cell(B, wa, v.j, v.tile, h);
                 mixed_home_cell<true, false>(B, wa, red);
             }
-            mixed_unit_end<true>(B, wa, v.j, v.tile, v.s_abs, lane);
+            mixed_unit_end<true>(B, wa, v.j, v.tile, v.s_abs, v.rel, lane);
         }
         __threadfence();
         __syncwarp();
