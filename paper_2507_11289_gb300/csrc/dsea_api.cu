@@ -1357,7 +1357,8 @@ int estimate_box_bytes(const dsea_box_desc *desc, const dsea_params *params, siz
     const size_t per_slot = 3 * sizeof(double) + (p.precision == DSEA_MIXED ? 3 * sizeof(float) + sizeof(float4)
                                                                             : sizeof(int) + 3 * sizeof(double));
     size_t b = 2 * ((size_t)hb.n_cells * 2 * sizeof(unsigned long long) + (size_t)hb.n_slots * per_slot);
-    b += (size_t)hb.n_cells * 3 * sizeof(double);              // unit partials
+    b += (size_t)hb.n_cells * dsea::kObsStride * sizeof(double);   // per-cell observable partials
+    if (p.temperature > 0.0) b += (size_t)hb.n_cells * 4 * sizeof(double);   // thermostat partials
     b += (size_t)desc->n_atoms * 9 * sizeof(double);           // read-back arrays
     b += 64 * 1024;                                            // descriptors, counters, plans
     *bytes = b;

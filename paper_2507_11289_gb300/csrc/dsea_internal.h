@@ -21,7 +21,7 @@ namespace dsea {
 constexpr int kThreads = 256;            // threads per work-unit CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxStagedCells = 2048;    // staged neighbourhood cells per unit (upper bound)
-constexpr int kObsStride = 4;            // unit partials of a force pass: U, W, KE, atom count
+constexpr int kObsStride = 4;            // per-cell partials of a force pass: U, W, KE, atom count
 
 // Device error word values (first error wins).
 enum : int {
@@ -79,7 +79,8 @@ struct BoxDev {
     int *err;             // device error word
     double *unit_obs;     // [n_cells * kObsStride] (U, W, KE, N) of each home cell, from a force pass
     // slice thermostat (T0 > 0): per unit (KE, N) of the synchronised velocities before
-    // scaling, and per slice the factor applied, both by step parity
+    // scaling (KE as an int64 fixed-point word), and per slice the factor of the step,
+    // both by step parity
     double T0;
     double *th_part[2];   // [units_per_step * 2]
     double *th_lam[2];    // [n_slices]

@@ -591,7 +591,6 @@ __device__ void run_unit_f64(const BoxDev &B, int j, int tile, long long s_abs, 
     int *s_start = reinterpret_cast<int *>(smem + Ly.start);
     int *s_gcell = reinterpret_cast<int *>(smem + Ly.gcell);
     int *s_slot = reinterpret_cast<int *>(smem + Ly.slot);
-    double *s_red = reinterpret_cast<double *>(smem + Ly.red);
     double *s_cellke = reinterpret_cast<double *>(smem + Ly.cellke);
     double *s_lam = reinterpret_cast<double *>(smem + Ly.lam);
     float *s_band = reinterpret_cast<float *>(smem + Ly.band);

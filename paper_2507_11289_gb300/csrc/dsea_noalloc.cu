@@ -7,7 +7,7 @@
 // latency-bound loop where cudaMalloc / cudaFree would synchronise the device
 // and stall every other stream.  For them, dsea_forces_noalloc runs the same
 // binning and force-pass kernels as a box does, but takes all of its scratch
-// (cell slots, counts, unit partials, the box descriptor) from one fixed,
+// (cell slots, counts, per-cell partials, the box descriptor) from one fixed,
 // file-scope device array instead of allocating it.  The caller passes the
 // inputs and outputs.
 //
