@@ -186,7 +186,7 @@ def time_box(dsea, torch, spec, precision, steps, warmup, md_steps, flush_buf, s
 
 
 def measured_peaks() -> dict:
-    """The measured peaks of this GPU pool (HBM copy GB/s, bf16 TFLOP/s), if present."""
+    """The peaks measured on this GPU model (HBM copy GB/s, bf16 TFLOP/s), if present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
