@@ -165,3 +165,33 @@ def test_thermostat_box_in_a_batch_equals_alone(precision, melted_4k):
     finally:
         for b in boxes:
             b.close()
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_fp64_nvt_two_layer_slices_anisotropic_box(walls):
+    """The slice thermostat where each slice holds two cell layers, in a box
+    with three different edges and cell counts (6 x 4 x 3 cells): 60 FP64
+    steps and the per-slice profiles against the oracle's."""
+    box = np.array([21.7, 13.4, 10.6])
+    g = [np.arange(k) * (L / k) + 0.25 for k, L in zip((18, 11, 9), box)]
+    pos = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = inputs.jitter(pos, box, 0.08, seed=43)
+    vel = inputs.maxwell_boltzmann(len(pos), 0.9, seed=44)
+    T0 = 1.4
+    with dsea.Box(pos, vel, box, n_slices=3, precision=dsea.FP64, temperature=T0, walls=walls) as b:
+        ncx, cps = slices_of(b)
+        assert (ncx, cps) == (6, 2)
+        b.advance(60)
+        rg, vg = b.positions(), b.velocities()
+        pg = b.profiles()
+    ro, vo, Fo, obs, st = oracle.run_nvt(pos, vel, box, 60, ncx, cps, T0, walls=walls)
+    d = rg - ro
+    d[:, 1:] = min_image(d[:, 1:], box[1:])
+    if not walls:
+        d[:, 0] -= box[0] * np.round(d[:, 0] / box[0])
+    dr, dv = np.abs(d).max(), np.abs(vg - vo).max()
+    print(f"NVT FP64, two-layer slices, walls {walls}: max |dr| {dr:.3e}, max |dv| {dv:.3e}")
+    assert dr <= 1e-9 and dv <= 1e-8
+    po = oracle.profiles(rg, vg, box, ncx, cps, walls=walls)
+    assert np.array_equal(pg["N"], po[:, 3].astype(np.int64))
+    assert np.allclose(pg["KE"], po[:, 2], rtol=1e-10)

@@ -368,6 +368,43 @@ def test_large_cells_many_chunks_and_windows(precision):
             assert np.abs(min_image(b.positions() - ro, box)).max() <= 1e-9
 
 
+
+@pytest.mark.parametrize("precision", [dsea.FP64, dsea.MIXED])
+@pytest.mark.parametrize("walls", [False, True])
+def test_anisotropic_box_with_two_layer_slices(precision, walls):
+    """Three different edges and cell counts (6 x 4 x 3 cells of 3.62 x 3.35 x
+    3.53) and three slices of two cell layers each, periodic or with mirror
+    walls along x: forces against the oracle, then 40 steps.  FP64: positions
+    to 1e-9 of the oracle's; mixed: forces at the GPU's own end positions to
+    2e-6 of the rms force."""
+    box = np.array([21.7, 13.4, 10.6])
+    g = [np.arange(k) * (L / k) + 0.25 for k, L in zip((18, 11, 9), box)]   # spacing 1.18-1.22
+    pos = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1).reshape(-1, 3)
+    pos = inputs.jitter(pos, box, 0.08, seed=41)
+    vel = inputs.maxwell_boltzmann(len(pos), 1.2, seed=42)
+    Fo, _, _ = oracle.forces(pos, box, RC, "cells", walls=walls)
+    tol = 1e-12 if precision == dsea.FP64 else 2e-6
+    with dsea.Box(pos, vel, box, n_slices=3, precision=precision, walls=walls) as b:
+        inf = b.info()
+        assert (inf["n_slices"], inf["cells_per_slice_x"], list(inf["cells"])) == (3, 2, [6, 4, 3])
+        e0, _ = force_err(b.forces(), Fo)
+        b.advance(40)
+        rg, Fg = b.positions(), b.forces()
+    print(f"precision {precision} walls {walls}: force error rms {e0:.3e} of rms force")
+    assert e0 <= tol
+    if precision == dsea.FP64:
+        ro, _, _, _ = oracle.run(pos, vel, box, steps=40, walls=walls)
+        d = rg - ro
+        d[:, 1:] -= box[1:] * np.round(d[:, 1:] / box[1:])
+        if not walls:
+            d[:, 0] -= box[0] * np.round(d[:, 0] / box[0])
+        assert np.abs(d).max() <= 1e-9
+    else:
+        Fe, _, _ = oracle.forces(rg, box, RC, "cells", walls=walls)
+        e1, _ = force_err(Fg, Fe)
+        print(f"  after 40 steps, at the GPU's positions: rms {e1:.3e}")
+        assert e1 <= 2e-6
+
 def _sparse_gas(n, box, dmin, seed):
     """n atoms uniform in the box, no two closer than dmin (minimum image)."""
     rng = np.random.Generator(np.random.PCG64(seed))
