@@ -463,3 +463,32 @@ def test_corner_and_edge_neighbours_near_the_cutoff(precision):
                 assert abs(Ug - Uo) <= 10 * tol * 4.0 * d ** -6
             else:
                 assert np.all(Fg == 0.0) and Ug == 0.0
+
+
+@pytest.mark.parametrize("rho", [0.05, 0.1, 0.2, 0.25, 0.3, 0.45, 0.6, 0.75, 0.9])
+def test_mixed_force_error_across_densities(rho):
+    """The mixed form's per-step force bar across the densities of the batched
+    and served workloads (0.05-0.9).  Below rho = 0.77 the cells grow toward
+    1.5 rc, so the FP32 coordinates of a neighbourhood grow with them.  Forces
+    of a jittered fcc start, then at the GPU's own positions after 100 mixed
+    steps at T 2.0, against the oracle at the same positions."""
+    pos, box = inputs.fcc_lattice(12, rho)                 # 6,912 atoms
+    pos = inputs.jitter(pos, box, 0.1, seed=51)
+    vel = inputs.maxwell_boltzmann(len(pos), 2.0, seed=52)
+    Fo, _, _ = oracle.forces(pos, box, RC, "cells")
+    with dsea.Box(pos, vel, box, precision=dsea.MIXED) as b:
+        edge = b.info()["cell_edge"]
+        F0 = b.forces()
+        b.advance(100)
+        rg, Fg = b.positions(), b.forces()
+    if rms(Fo) == 0.0:   # rho 0.05: the fcc spacing (3.05) exceeds rc, no pair in range
+        assert np.all(F0 == 0.0)
+        e0, m0 = 0.0, 0.0
+    else:
+        e0, m0 = force_err(F0, Fo)
+    Fe, _, _ = oracle.forces(rg, box, RC, "cells")
+    assert rms(Fe) > 0.0
+    e1, m1 = force_err(Fg, Fe)
+    print(f"rho {rho}: cell edge {edge[0]:.3f}; force error rms {e0:.3e} (max {m0:.2e}), "
+          f"after 100 steps rms {e1:.3e} (max {m1:.2e})")
+    assert e0 <= 2e-6 and e1 <= 2e-6
