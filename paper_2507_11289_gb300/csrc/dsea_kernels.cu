@@ -1055,7 +1055,7 @@ constexpr int kHomeMax = 128;                 // largest cell capacity (slots of
 // once per home cell and read back through volatile loads where they are
 // needed, so that no register holds them across the pair loop.
 struct WarpArea {
-    float4 list[kListAtoms];   // kListAtoms / 2 entry pairs: [x0 x1 y0 y1], [z0 z1 id0 id1]
+    float4 list[kListAtoms];   // kListAtoms / 2 entry pairs: [x0 x1 y0 y1], [z0 z1 w0 w1] (w: home atoms' ids)
     unsigned char hslot[kHomeMax];   // slot of each home atom within its cell, canonical order
     long long s_abs;           // step of the input state
     long long hcell;           // home cell
@@ -1251,7 +1251,9 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
     // been masked to zero.  Kept entries are compacted in order into the
     // pair layout, in place: an entry never moves up, and each 64-entry
     // sweep (two entries per lane, which overlaps their loads and tests) writes
-    // below the entries the next sweep reads.
+    // below the entries the next sweep reads.  Only x, y and z are stored: a
+    // neighbour's w (its tag) is not read again; the home atoms' ids come
+    // from the home segment.
     const float reach2 = B.rc2f + kReachMargin;
     const unsigned below = (1u << lane) - 1u;
     int m = k0;
@@ -1274,19 +1276,19 @@ __device__ __forceinline__ void build_window(const BoxDev &B, int p, const NbrCe
         __syncwarp();
         if (ka && idx_ok(B.err, m + __popc(kA & below), kListAtoms)) {
             float *d = list_entry(wa, m + __popc(kA & below));
-            d[0] = a.x; d[2] = a.y; d[4] = a.z; d[6] = a.w;
+            d[0] = a.x; d[2] = a.y; d[4] = a.z;
         }
         m += __popc(kA);
         if (kb && idx_ok(B.err, m + __popc(kB & below), kListAtoms)) {
             float *d = list_entry(wa, m + __popc(kB & below));
-            d[0] = b.x; d[2] = b.y; d[4] = b.z; d[6] = b.w;
+            d[0] = b.x; d[2] = b.y; d[4] = b.z;
         }
         m += __popc(kB);
     }
     if (m & 1) {   // pad the window to whole pairs
         if (lane == 0) {
             float *d = list_entry(wa, m);
-            d[0] = kFarAway; d[2] = kFarAway; d[4] = kFarAway; d[6] = 0.f;
+            d[0] = kFarAway; d[2] = kFarAway; d[4] = kFarAway;
         }
         ++m;
     }
