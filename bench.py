@@ -483,7 +483,7 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -518,6 +518,11 @@ def main():
                     help="comma list of legs to skip: fp64,walls,nvt,67m,batch,serve,dataset,cpu,e2e")
     ap.add_argument("--walls-steps", type=int, default=3, help="timed steps of the mirror-wall leg")
     ap.add_argument("--nvt-steps", type=int, default=3, help="timed steps of the thermostat leg")
+    return ap
+
+
+def main():
+    ap = build_parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
