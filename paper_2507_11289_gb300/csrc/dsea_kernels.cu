@@ -1846,9 +1846,15 @@ __global__ void __launch_bounds__(1024) k_obs_reduce(const double *cell_obs, lon
 // Sec. 3.1 / Table 1).  A CTA only waits on tickets smaller than its own, all
 // of which were taken by running CTAs, so the ring always progresses.
 #ifndef DSEA_RING_MIN_BLOCKS
-#define DSEA_RING_MIN_BLOCKS 4   // CTAs per SM the register allocation must allow
+#define DSEA_RING_MIN_BLOCKS 4   // CTAs per SM the register allocation must allow (mixed form)
 #endif
-__global__ void __launch_bounds__(kThreads, DSEA_RING_MIN_BLOCKS) k_ring_f64(RingPlan plan)
+// The FP64 unit's staging and force queues fill enough shared memory that an SM
+// holds two of its CTAs, so its registers are budgeted for two (128 per thread)
+// rather than spilled to fit four.
+#ifndef DSEA_RING_F64_MIN_BLOCKS
+#define DSEA_RING_F64_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(kThreads, DSEA_RING_F64_MIN_BLOCKS) k_ring_f64(RingPlan plan)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ BoxDev sB;
